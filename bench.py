@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the multi-determinant table method: walker-moves per second.
+
+One step = one single-electron move of every walker: propose r' = r + tau * eta,
+msd_ratio (ratio, gradient and laplacian at r'), Metropolis test, msd_accept
+(Sherman-Morrison update), plus the amortised from-scratch refresh of each spin every
+K = 64 of its steps and the CI contraction when the moving spin changes.  Electrons
+move in index order, so 128 steps are one sweep.
+
+Default workload (64 + 64 electrons, 256 orbitals per spin, 144 Gaussians, 1e5
+determinants with excitation orders 1-8, 4096 walkers), synthetic and seeded.  The
+headline value is the mixed-precision path; the same line reports the FP64 path, the
+per-result difference between the two, the excitation-sweep kernel's roofline
+fraction, an end-to-end number through the host-buffer C ABI, and the FP64 CPU oracle
+timed on a bounded sample (walker-moves of one walker) on this machine's cores.
+
+--impl reference times the oracle alone (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "walker-moves/sec (ratio+grad+lap) at 128 e-, 1e5 dets; mixed vs FP64, % roofline"
+UNIT = "walker-moves/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64 ALU nominal rate of GB300 (no FP64 tensor path is used)
+FP64_ALU_TFLOPS = 1.25
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ----------------------------------------------------------------------------------------
+# work model of the excitation-sweep kernel (one launch = all walkers, one moved electron)
+# ----------------------------------------------------------------------------------------
+def sweep_work(problem, spin: int, W: int, mixed: bool):
+    """Algorithmic flops and HBM bytes of one excitation-sweep launch.
+
+    Per walker: sum_k n_k ((2/3) k^3 + 2 k^2 + 10 k + 10) flops for the excitations (one
+    shared LU of T_u, one solve, five bordered channels, five CI multiply-adds), plus
+    10 n m for the five virtual-row contractions and 10 n for rho and s^a.  Bytes per
+    walker: the C stream (n_exc values), the table T (n m values), the column of A_0^{-1},
+    the five orbital rows at r', and the y row written for the accept step; the shared
+    excitation lists once per launch.
+    """
+    n, N = problem.n_elec[spin], problem.n_orb[spin]
+    m = N - n
+    k = problem.exc_orders(spin)
+    hist = np.bincount(k, minlength=9)
+    f = sum(int(hist[q]) * ((2.0 / 3.0) * q ** 3 + 2 * q * q + 10 * q + 10) for q in range(1, 9))
+    f += 5 * int(hist[0]) * 2
+    f += 10.0 * n * m + 10.0 * n
+    b = 4 if mixed else 8
+    per_walker = problem.n_exc(spin) * b + n * m * b + n * 8 + 5 * N * b + m * b + 6 * 8
+    lists = sum(int(hist[q]) * (2 if q <= 1 else 4 if q == 2 else 8 if q <= 4 else 16) for q in range(1, 9))
+    return f * W, per_walker * W + lists
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while running; summarised over a time window."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(device_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self, t0: float, t1: float):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[5:10]))
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25]
+        if not inside:
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:2]
+        names = ("active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(names[1:], r[3][1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------------------
+# the oracle arm (CPU, FP64, every determinant by LU)
+# ----------------------------------------------------------------------------------------
+def oracle_rate(wl, n_moves: int, time_cap: float):
+    """Walker-moves/s of the FP64 oracle on one walker: each move evaluates Psi, grad and
+    lap at the proposed position from scratch and takes the ratio to the stored Psi."""
+    import oracle as orc
+
+    o = orc.Oracle(wl.problem)
+    R = wl.R0[:1].copy()
+    cur = o.eval(R)
+    eta, u = wl.proposals(max(n_moves, 1), seed_offset=99)
+    done = 0
+    t0 = time.perf_counter()
+    for t in range(n_moves):
+        e = t % wl.problem.n_tot
+        rnew = R[:, e] + wl.tau * eta[t, :1]
+        ratio, new = o.ratio(R, e, rnew, cur)
+        if u[t, 0] < ratio[0] ** 2:
+            R[0, e] = rnew[0]
+            cur = dict(logabs=new["logabs"], sign=new["sign"])
+        done += 1
+        if time.perf_counter() - t0 > time_cap:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, orc.num_threads()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1106_2456_gb300 import workloads
+
+    wl = workloads.make_workload(args.workload, n_walkers=2)
+    warm = min(args.warmup, 1)
+    if warm:
+        oracle_rate(wl, warm, 60.0)
+    rate, done, dt, cores = oracle_rate(wl, args.steps, args.ref_time_cap)
+    sample = (f"{done} single-walker moves (ratio + grad + lap, every determinant by LU) of the "
+              f"{args.workload} workload, {dt:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws, "steps": done,
+            "warmup": warm, "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "walkers_per_step": 1, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# the CUDA arm
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1106_2456_gb300 import msd, workloads
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build() if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    msd.load_library()
+    peaks, peak_kind = load_peaks()
+    wl = workloads.make_workload(args.workload)
+    p = wl.problem
+    W = wl.n_walkers
+    K = wl.refresh_K
+    n_tot = p.n_tot
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(4242 + rank)
+    R0 = wl.R0 + (0.01 * rng.standard_normal(wl.R0.shape) if rank else 0.0)
+    total = args.warmup + args.steps
+    eta_np, u_np = wl.proposals(total, seed_offset=rank)
+    eta = torch.tensor(eta_np, device=dev)
+    u = torch.tensor(u_np, device=dev)
+
+    def make(prec):
+        c = msd.MSD(p, W, prec, refresh_K=K, stream=stream)
+        c.set_positions(torch.tensor(R0, device=dev))
+        return c
+
+    bufs = dict(rnew=torch.empty(W, 3, dtype=torch.float64, device=dev),
+                ratio=torch.empty(W, dtype=torch.float64, device=dev),
+                grad=torch.empty(W, 3, dtype=torch.float64, device=dev),
+                lap=torch.empty(W, dtype=torch.float64, device=dev),
+                acc=torch.empty(W, dtype=torch.uint8, device=dev))
+
+    def step(c, t):
+        e = t % n_tot
+        c.propose(e, eta[t], wl.tau, bufs["rnew"])
+        c.ratio_into(e, bufs["rnew"], bufs["ratio"], bufs["grad"], bufs["lap"])
+        c.metropolis(u[t], bufs["ratio"], bufs["acc"])
+        c.accept(e, bufs["acc"])
+
+    def timed(c, steps):
+        for t in range(args.warmup):
+            step(c, t)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if rank == 0 else None
+        time.sleep(0.3 if clk else 0)
+        c.timing_start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        e0.record(stream)
+        for t in range(args.warmup, args.warmup + steps):
+            step(c, t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        sweep_ms, n_sweep, n_launch = c.timing_stop()
+        if clk:
+            clk.stop()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        c.sync()
+        return ms, sweep_ms, n_sweep, n_launch, (clk.summary(w0, w1) if clk else None)
+
+    def roofline(prec, sweep_ms, steps):
+        mixed = prec == "mixed"
+        F = B = 0.0
+        for t in range(args.warmup, args.warmup + steps):
+            s = p.spin_of(t % n_tot)
+            f, b = sweep_work(p, s, W, mixed)
+            F += f
+            B += b
+        sec = sweep_ms * 1e-3
+        hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+        alu_peak = FP32_ALU_TFLOPS if mixed else FP64_ALU_TFLOPS
+        t_alu = F / (alu_peak * 1e12)
+        t_hbm = B / (hbm_peak * 1e9)
+        hbm = {"achieved": B / sec / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": B / sec / 1e9 / hbm_peak,
+               "peak_source": peak_kind}
+        alu = {"achieved": F / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s", "frac": F / sec / 1e12 / alu_peak,
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if mixed
+               else "nominal GB300 FP64 rate"}
+        main = dict(alu if t_alu >= t_hbm else hbm)
+        main["bound"] = "alu" if t_alu >= t_hbm else "hbm"
+        main["traffic"] = None
+        main["kernel"] = "k_ratio (excitation sweep, steps A2-A5)"
+        main["launches"] = steps
+        main["avg_launch_us"] = 1e3 * sweep_ms / steps
+        main["other"] = hbm if main["bound"] == "alu" else alu
+        return main
+
+    # ---- mixed precision (headline) ----
+    cm = make("mixed")
+    ms, sweep_ms, n_sweep, n_launch, clocks = timed(cm, args.steps)
+    value = W * ws * args.steps / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {p.n_elec[0]}+{p.n_elec[1]} electrons, {p.n_orb[0]} orbitals "
+                                   f"per spin, {p.n_basis} Gaussians, {p.n_det} determinants "
+                                   f"({p.n_exc(0)}+{p.n_exc(1)} unique strings), {W} walkers per GPU, "
+                                   f"refresh every {K} steps of a spin",
+                       "precision": "mixed: FP32 orbitals/table/excitation dets, FP64 inverse/SM/ratio sums",
+                       "walkers_per_gpu": W, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs exceed L2 (per-walker tables and CI streams: >1 GB)"},
+            "roofline": roofline("mixed", sweep_ms, args.steps),
+            "gpu_launches": int(n_launch), "clocks": clocks}
+    # ---- end to end through the host-buffer C ABI ----
+    if args.e2e_steps > 0:
+        e2e_steps = min(args.steps, args.e2e_steps)
+        Rh, _, _ = cm.get_state()
+        Rh = Rh.cpu().numpy()
+        eta_h = eta_np
+        u_h = u_np
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+        rnew_h, ratio_h = pin((W, 3), torch.float64), pin((W,), torch.float64)
+        grad_h, lap_h, acc_h = pin((W, 3), torch.float64), pin((W,), torch.float64), pin((W,), torch.uint8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        base = args.warmup + args.steps
+        for q in range(e2e_steps):
+            t = (base + q) % total
+            e = (base + q) % n_tot
+            np.add(Rh[:, e], wl.tau * eta_h[t], out=rnew_h)
+            cm.ratio_host(e, rnew_h, ratio_h, grad_h, lap_h)
+            np.less(u_h[t], ratio_h * ratio_h, out=acc_h, casting="unsafe")
+            cm.accept_host(e, acc_h)
+            sel = acc_h.astype(bool)
+            Rh[sel, e] = rnew_h[sel]
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([dt], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        line["e2e"] = {"value": W * ws * e2e_steps / dt, "unit": UNIT, "steps": e2e_steps,
+                       "h2d_bytes_per_step": W * 3 * 8 + W, "d2h_bytes_per_step": W * 5 * 8,
+                       "path": "msd_ratio_host + msd_accept_host (pinned host buffers, synchronous)"}
+    # ---- FP64 path on the same workload ----
+    if not args.skip_fp64:
+        cm.close()
+        cd = make("fp64")
+        steps64 = min(args.steps, args.fp64_steps)
+        ms64, sweep64, _, _, clk64 = timed(cd, steps64)
+        line["fp64"] = {"value": W * ws * steps64 / (ms64 * 1e-3), "ms_per_step": ms64 / steps64, "steps": steps64,
+                        "roofline": roofline("fp64", sweep64, steps64), "clocks": clk64}
+        line["mixed_speedup_vs_fp64"] = value / line["fp64"]["value"]
+        # per-result difference mixed vs FP64 on a common trajectory (FP64 accept decisions)
+        cd.set_positions(torch.tensor(R0, device=dev))
+        cm = make("mixed")
+        errs = {"ratio": [], "grad": [], "lap": []}
+        for t in range(args.cmp_steps):
+            e = t % n_tot
+            cd.propose(e, eta[t], wl.tau, bufs["rnew"])
+            r64, g64, l64 = cd.ratio(e, bufs["rnew"])
+            r32, g32, l32 = cm.ratio(e, bufs["rnew"])
+            for key, a, b in (("ratio", r32, r64), ("grad", g32, g64), ("lap", l32, l64)):
+                rel = ((a - b).abs() / b.abs().clamp_min(1e-300)).flatten().cpu().numpy()
+                errs[key].append(rel)
+            cd.metropolis(u[t], r64, bufs["acc"])
+            cd.accept(e, bufs["acc"])
+            cm.accept(e, bufs["acc"])
+        line["mixed_vs_fp64"] = {k: {"median_rel": float(np.median(np.concatenate(v))),
+                                     "p99_rel": float(np.percentile(np.concatenate(v), 99))}
+                                 for k, v in errs.items()}
+        line["mixed_vs_fp64"]["steps"] = args.cmp_steps
+        cd.close()
+    cm.close()
+    # ---- FP64 CPU oracle on a bounded sample ----
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        rate, done, dt, cores = oracle_rate(wl, args.cpu_moves, args.cpu_time_cap)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{done} single-walker moves of this workload (every determinant and "
+                                          f"derivative determinant by LU, FP64), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=512)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large")
+    ap.add_argument("--fp64-steps", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=128)
+    ap.add_argument("--cmp-steps", type=int, default=16)
+    ap.add_argument("--cpu-moves", type=int, default=6)
+    ap.add_argument("--cpu-time-cap", type=float, default=25.0)
+    ap.add_argument("--ref-time-cap", type=float, default=150.0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * msd.h -- C ABI of libmsd: the multi-Slater-determinant "table method"
+ * (Clark, Morales, McMinis, Kim, Scuseria, arXiv:1106.2456) on one NVIDIA GB300 GPU.
+ *
+ * Wavefunction (Section II):   Psi(R) = sum_I c_I det M_up,I(R) det M_dn,I(R),
+ *   M_s,I(r, c) = phi_{col_I(c)}(r_r)  -- rows are electrons, columns orbitals.
+ * Orbitals 0..n_s-1 of spin s form the reference determinant M_s,0; orbitals
+ * n_s..N_s-1 are the m_s = N_s - n_s virtuals.  An excitation string of order k
+ * replaces the occupied columns h_1 < ... < h_k IN PLACE by the virtual orbitals
+ * n_s + p_1 < ... < n_s + p_k (column h_q holds orbital n_s + p_q).
+ *
+ * Per walker the library keeps, for each spin, A_0^{-1} (FP64) and the excitation
+ * table T = A_0^{-1} Phi_virt (Section III, Algorithm 1 step 3), and computes
+ *   - the ratio Psi(R') / Psi(R) of a single-electron move (Section II and III):
+ *     every excitation ratio det A_u / det A_0 is the k x k determinant of the table
+ *     entries T[h_q, p_l] (Section III), bordered by the moved electron's row;
+ *   - grad_i Psi / Psi and lap_i Psi / Psi at the proposed position (Section IV-A:
+ *     the same table with the electron's row replaced by derivative rows);
+ *   - the Sherman-Morrison update of A_0^{-1} and T on acceptance (Section III,
+ *     Algorithm 1 step 1), and a from-scratch refresh every refresh_K steps
+ *     (Section III: "calculated from scratch").
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are DEVICE pointers, read and written in stream order on
+ *     the context's CUDA stream; the call returns before the GPU work completes.
+ *     Pointers named *_host are HOST pointers; those calls synchronise.
+ *   - Arrays are C-contiguous (row-major) with the stated shapes; W = n_walkers.
+ *     Walker positions are [W][n_up + n_dn][3] doubles in bohr, up electrons first.
+ *   - No call allocates after msd_init, except msd_eval_batch on first use (it
+ *     creates a second walker state so that the main one is left untouched).
+ *   - Device-side numerical faults (a zero or non-finite pivot, a non-finite ratio)
+ *     set a status word that msd_sync reports; host-side argument errors return
+ *     MSD_ERR_ARG and leave the context unchanged.  msd_last_error explains the
+ *     last failure.  No call throws.  A context is used by one host thread at a time.
+ */
+#ifndef MSD_H
+#define MSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSD_MAX_ORDER 8   /* largest per-spin excitation order (Section III: "less then 8") */
+#define MSD_MAX_ORB 256   /* holes and particles are stored as uint8 */
+
+typedef enum {
+    MSD_OK = 0,
+    MSD_ERR_ARG = 1,       /* invalid argument; nothing was done */
+    MSD_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    MSD_ERR_OOM = 3,       /* device allocation failed */
+    MSD_ERR_SINGULAR = 4,  /* a reference determinant or a ratio was zero or not finite */
+    MSD_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    MSD_ERR_STATE = 6      /* call out of order (e.g. msd_accept without msd_ratio) */
+} msd_status;
+
+typedef enum {
+    MSD_FP64 = 0,   /* every step in FP64 */
+    MSD_MIXED = 1   /* orbitals, table and excitation determinants in FP32; A_0^{-1},
+                       its Sherman-Morrison update, the refresh LU, log|det| and the
+                       final CI sums in FP64 */
+} msd_precision;
+
+/*
+ * Problem description (host arrays, copied by msd_init; the caller keeps ownership).
+ * Basis functions are unnormalised Cartesian Gaussians (r - A)^l exp(-alpha |r - A|^2)
+ * with l <= 1; phi_j(r) = sum_mu chi_mu(r) B_s[mu][j].
+ */
+typedef struct {
+    int32_t n_elec[2];            /* electrons per spin (n_up, n_dn), each 1..MSD_MAX_ORB */
+    int32_t n_orb[2];             /* orbitals per spin N_s >= n_s, N_s - n_s <= MSD_MAX_ORB */
+    int32_t n_nuc;
+    const double* nuc_xyz;        /* [n_nuc][3] bohr */
+    int32_t n_basis;
+    const int32_t* bas_center;    /* [n_basis] nucleus index */
+    const int8_t* bas_lm;         /* [n_basis] 0 = s, 1 = px, 2 = py, 3 = pz */
+    const double* bas_alpha;      /* [n_basis] exponent > 0 */
+    const double* B[2];           /* per spin [n_basis][n_orb[s]]; B[1] == B[0] allowed */
+    int32_t n_exc[2];             /* unique excitation strings per spin, >= 1 */
+    const int32_t* exc_off[2];    /* [n_exc + 1] CSR offsets; string u has order
+                                     exc_off[u+1] - exc_off[u] <= MSD_MAX_ORDER;
+                                     string 0 must be the reference (order 0) */
+    const uint8_t* exc_holes[2];  /* strictly ascending occupied indices < n_elec[s] */
+    const uint8_t* exc_parts[2];  /* strictly ascending virtual indices < n_orb[s] - n_elec[s] */
+    int64_t n_det;                /* number of terms I, >= 1 */
+    const int32_t* det_up;        /* [n_det] spin-up string of term I */
+    const int32_t* det_dn;        /* [n_det] spin-down string of term I */
+    const double* ci;             /* [n_det] c_I */
+    int32_t n_walkers;            /* W >= 1 */
+    msd_precision prec;
+    int32_t refresh_K;            /* recompute A_0^{-1} and T of a spin from scratch after
+                                     this many proposed moves of that spin (>= 1) */
+    void* cuda_stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+} msd_problem;
+
+typedef struct msd_ctx msd_ctx;
+
+/* Create a context for n_systems problems (only n_systems == 1 is accepted by this
+ * build; batched uneven systems return MSD_ERR_ARG).  Validates every array, reorders
+ * the excitation strings by order (and lexicographically within an order) for the
+ * device, and allocates all per-walker state.  *out is NULL on failure. */
+msd_status msd_init(const msd_problem* prob, int32_t n_systems, msd_ctx** out);
+
+/* Set the walker positions R_dev [W][n_tot][3] and build the state from scratch:
+ * orbitals, LU of A_0 (A_0^{-1}, log|det A_0|, sign), T = A_0^{-1} Phi_virt and the CI
+ * sums (Section III: initial inverse and determinants computed from scratch). */
+msd_status msd_set_positions(msd_ctx* ctx, const double* R_dev);
+
+/* Propose moving electron `elec` (0..n_tot-1) of every walker to rnew_dev [W][3].
+ * Writes ratio_dev [W] = Psi(R') / Psi(R) and, if non-NULL, grad_dev [W][3] =
+ * grad_elec Psi(R') / Psi(R') and lap_dev [W] = lap_elec Psi(R') / Psi(R') (both at the
+ * proposed position).  grad_dev and lap_dev must be both NULL or both non-NULL.  No
+ * walker state changes; the proposal is kept for msd_accept.  Runs Algorithm 1 in the
+ * bordered form: one table-row contraction y = phi_virt(r') - T^T phi_occ(r') per
+ * channel and one (k+1) x (k+1) bordered determinant per excitation and channel. */
+msd_status msd_ratio(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev,
+                     double* grad_dev, double* lap_dev);
+
+/* Apply the last msd_ratio proposal (which must be for `elec`) to the walkers whose
+ * accept_dev [W] byte is non-zero: Sherman-Morrison update of A_0^{-1} (FP64), rank-1
+ * update of T, log|det A_0| and sign, the stored CI sum, and the position. */
+msd_status msd_accept(msd_ctx* ctx, int32_t elec, const uint8_t* accept_dev);
+
+/* grad_elec Psi / Psi [W][3] and lap_elec Psi / Psi [W] at the current positions.
+ * elec = -1 evaluates every electron: grad_dev [W][n_tot][3], lap_dev [W][n_tot]. */
+msd_status msd_grad_lap(msd_ctx* ctx, int32_t elec, double* grad_dev, double* lap_dev);
+
+/* From scratch at positions R_dev [W][n_tot][3], without touching the walker state:
+ * log|Psi| [W], sign [W], and if non-NULL all-electron grad [W][n_tot][3] and
+ * lap [W][n_tot] (ratios of Psi, as in msd_grad_lap). */
+msd_status msd_eval_batch(msd_ctx* ctx, const double* R_dev, double* logabs_dev, double* sign_dev,
+                          double* grad_dev, double* lap_dev);
+
+/* Current walker state: positions R_dev [W][n_tot][3] (may be NULL), log|Psi| [W] and
+ * sign [W] (may be NULL), tracked through accepted moves. */
+msd_status msd_get_state(msd_ctx* ctx, double* R_dev, double* logabs_dev, double* sign_dev);
+
+/* Copy one piece of the per-walker state to dst_dev (device memory, stream-ordered), for
+ * checkpoints and diagnostics.  item: 0 = positions [W][n_tot][3] f64 (spin ignored),
+ * 1 = A_0^{-1} [W][n][n] f64 (A^{-1}[c][r]), 2 = table T [W][n][m], 3 = log|det A_0| [W] f64,
+ * 4 = sign of det A_0 [W] f64, 5 = S = Psi / (det A_up,0 det A_dn,0) [W] f64 (spin ignored),
+ * 6 = CI weights C [W][n_exc], 7 = excitation values t [W][n_exc]; the last msd_ratio
+ * proposal (spin ignored): 8 = rho [W] f64, 9 = sum_u C_u d^a_u [W][5] f64,
+ * 10 = y^0 [W][m of the moved spin], 11 = orbitals at r' [W][1 or 5][N of the moved spin].
+ * T, C, t, y^0 and the orbitals are f64 in MSD_FP64 and f32 in MSD_MIXED; C and t follow the
+ * library's internal string order and are only current right after the call that used
+ * them.  Returns the byte count in *bytes. */
+msd_status msd_copy_state(msd_ctx* ctx, int32_t item, int32_t spin, void* dst_dev, int64_t* bytes);
+
+/* Metropolis helpers of a VMC driver (Section II: a step moves one electron).
+ * msd_propose: rnew_dev [W][3] = R[w][elec] + tau * eta_dev [W][3].
+ * msd_metropolis: accept_dev [W] = (u_dev[w] < ratio_dev[w]^2) -- no Jastrow factor. */
+msd_status msd_propose(msd_ctx* ctx, int32_t elec, const double* eta_dev, double tau, double* rnew_dev);
+msd_status msd_metropolis(msd_ctx* ctx, const double* u_dev, const double* ratio_dev, uint8_t* accept_dev);
+
+/* Host-buffer twins of one walker-move, for callers without device memory: copy the
+ * inputs to the device, run, copy the results back, synchronise.
+ * msd_ratio_host: rnew_host [W][3] -> ratio_host [W], grad_host [W][3], lap_host [W].
+ * msd_accept_host: accept_host [W] bytes. */
+msd_status msd_ratio_host(msd_ctx* ctx, int32_t elec, const double* rnew_host, double* ratio_host,
+                          double* grad_host, double* lap_host);
+msd_status msd_accept_host(msd_ctx* ctx, int32_t elec, const uint8_t* accept_host);
+
+/* Change the CUDA stream used by later calls (cudaStream_t; NULL = legacy default). */
+msd_status msd_set_stream(msd_ctx* ctx, void* cuda_stream);
+
+/* Wait for the context's stream; report and clear the device status word. */
+msd_status msd_sync(msd_ctx* ctx);
+
+/* Human-readable description of the last failure of this context ("" if none).
+ * With ctx == NULL: the last msd_init failure of the calling thread. */
+const char* msd_last_error(const msd_ctx* ctx);
+
+/* Counts used by the benchmark's work model: out[0] = n_exc of spin s, out[1 + k] =
+ * number of strings of order k (k = 0..MSD_MAX_ORDER) of spin s. */
+msd_status msd_exc_histogram(const msd_ctx* ctx, int32_t spin, int64_t* out);
+
+/* Kernel timing for measurement.  msd_timing_start clears the counters and, from then on,
+ * brackets every launch of the excitation-sweep kernel (the one that runs steps A2-A5 of
+ * msd_ratio) with CUDA events on the context's stream and counts every kernel the library
+ * launches.  msd_timing_stop synchronises the stream, stops recording and returns the summed
+ * event time of those sweep launches (ms), their number, and the number of all kernel
+ * launches since msd_timing_start.  Any output pointer may be NULL. */
+msd_status msd_timing_start(msd_ctx* ctx);
+msd_status msd_timing_stop(msd_ctx* ctx, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void msd_destroy(msd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSD_H */

@@ -67,6 +67,7 @@ def _load():
         lib.orc_lu_logdet.argtypes = [i32, vp, vp, vp]
         lib.orc_basis.argtypes = [vp, vp, vp]
         lib.orc_orbitals.argtypes = [vp, i32, vp, vp]
+        lib.orc_slater.argtypes = [vp, i32, vp, vp]
         lib.orc_eval.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         lib.orc_eval.restype = i32
         lib.orc_eval_batch.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp]
@@ -146,6 +147,25 @@ class Oracle:
         r = np.ascontiguousarray(r, np.float64)
         self._lib.orc_orbitals(self._sp, spin, _ptr(r), _ptr(out))
         return out
+
+    def slater(self, spin: int, R) -> np.ndarray:
+        """Reference Slater matrix A_0[r, c] = phi_c(r_r) of one spin at configuration R [n_tot, 3]."""
+        n = self.p.n_elec[spin]
+        out = np.zeros((n, n))
+        R = np.ascontiguousarray(R, np.float64)
+        self._lib.orc_slater(self._sp, spin, _ptr(R), _ptr(out))
+        return out
+
+    def reference_condition(self, R, elec: Optional[int] = None, rnew=None) -> float:
+        """Largest 2-norm condition number of the reference matrices of both spins at R and, for a
+        move of electron elec to rnew, of the moved spin's reference matrix at R'.  Every quantity
+        the table method forms passes through A_0^{-1}, so its rounding errors scale with this."""
+        kap = max(np.linalg.cond(self.slater(s, R)) for s in range(2))
+        if elec is not None and elec >= 0 and rnew is not None:
+            R2 = np.array(R, dtype=np.float64, copy=True)
+            R2[elec] = rnew
+            kap = max(kap, np.linalg.cond(self.slater(self.p.spin_of(elec), R2)))
+        return float(kap)
 
     # -- wavefunction -----------------------------------------------------------------
     def eval(self, R: np.ndarray, elec: int = -1, rnew: Optional[np.ndarray] = None) -> Dict[str, np.ndarray]:

@@ -173,6 +173,18 @@ void orc_orbitals(const orc_problem* p, int s, const double* r, double* phi) {
     free(chi);
 }
 
+/* Reference Slater matrix of spin s at R: A0[r * n + c] = phi_c(r_r), c < n (Section II). */
+void orc_slater(const orc_problem* p, int s, const double* R, double* A0) {
+    const int n = p->n_elec[s], N = p->n_orb[s];
+    const int off = s ? p->n_elec[0] : 0;
+    double* tmp = (double*)malloc(sizeof(double) * 5 * (size_t)N);
+    for (int r = 0; r < n; ++r) {
+        orc_orbitals(p, s, R + 3 * (off + r), tmp);
+        memcpy(A0 + (size_t)r * n, tmp, sizeof(double) * n);
+    }
+    free(tmp);
+}
+
 /* Orbital index held by column c of the determinant of string u (in-place replacement). */
 static void string_columns(const orc_problem* p, int s, int u, int* cols) {
     const int n = p->n_elec[s];

@@ -1,0 +1,723 @@
+// msd_api.cu -- the C ABI of libmsd (declared in include/msd.h): validation, device layout of
+// the excitation strings, per-walker state and the order of kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "msd.h"
+#include "msd_internal.h"
+
+using namespace msd;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct SpinConst {
+    int n = 0, N = 0, m = 0, off = 0;
+    void* B = nullptr;            // [nb][N] (double or float)
+    ExcDev g;                     // device strings, grouped by order
+    std::vector<int> user_of;     // internal index -> user index
+    std::vector<int> internal_of; // user index -> internal index
+    std::vector<long long> hist;  // strings per order 0..MAXK
+    // terms grouped by this spin's internal string, used when this spin moves
+    int* t_off = nullptr;         // [n_exc + 1]
+    int* t_other = nullptr;       // [n_det] other spin's internal string
+    double* t_c = nullptr;        // [n_det]
+    int* heavy = nullptr;         // strings with many terms
+    int n_heavy = 0;
+};
+
+struct State {
+    bool alloc = false, ready = false;
+    double* R = nullptr;  // [W][n_tot][3]
+    double* S = nullptr;  // [W] sum_u C_s[u] t_s[u] = Psi / (det A_up,0 det A_dn,0)
+    double* Ainv[2] = {nullptr, nullptr};
+    void* T[2] = {nullptr, nullptr};
+    double* logdet[2] = {nullptr, nullptr};
+    double* sgn[2] = {nullptr, nullptr};
+    void* t[2] = {nullptr, nullptr};
+    void* C[2] = {nullptr, nullptr};
+    int since_refresh[2] = {0, 0};
+    bool C_valid[2] = {false, false};
+};
+
+}  // namespace
+
+struct msd_ctx {
+    int W = 0, n_tot = 0, nb = 0, K = 1;
+    bool mixed = false;
+    size_t tb = 8;  // bytes of the table/orbital type
+    cudaStream_t stream = nullptr;
+    double4* bas = nullptr;
+    int8_t* blm = nullptr;
+    SpinConst sp[2];
+    State st, scratch;
+    void* Phi = nullptr;       // [W][n_max][N_max] orbitals of all electrons of one spin
+    void* phi_new = nullptr;   // [W][NCH][N_max] orbitals at the proposed position
+    void* phi_tmp = nullptr;   // [W][NCH][N_max] orbitals for msd_grad_lap / eval_batch
+    double* rho = nullptr;     // [W]
+    double* num = nullptr;     // [W][NCH]
+    void* y0 = nullptr;        // [W][m_max]
+    double* rnew = nullptr;    // [W][3]
+    double* dummy = nullptr;   // [W] discarded ratios
+    int prop_elec = -1, prop_nch = 0;
+    bool prop_valid = false;
+    int* d_status = nullptr;
+    // staging for the host-buffer entry points
+    double* d_io = nullptr;    // [W][8]
+    uint8_t* d_acc = nullptr;  // [W]
+    std::vector<void*> allocs;
+    std::string err;
+    // measurement: kernel launch count and events around the excitation-sweep kernel
+    bool timing = false;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev;  // pairs (begin, end)
+    size_t ev_used = 0;
+    Launch L() { return Launch{stream, d_status, timing ? &launches : nullptr}; }
+    Launch L_sweep() {
+        Launch l = L();
+        if (timing) {
+            if (ev_used + 2 > ev.size()) {
+                for (int i = 0; i < 2; ++i) {
+                    cudaEvent_t e = nullptr;
+                    cudaEventCreate(&e);
+                    ev.push_back(e);
+                }
+            }
+            l.t0 = ev[ev_used];
+            l.t1 = ev[ev_used + 1];
+            ev_used += 2;
+        }
+        return l;
+    }
+};
+
+namespace {
+
+msd_status fail(msd_ctx* c, msd_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return s;
+}
+
+msd_status check_launch(msd_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+template <typename T>
+msd_status dalloc(msd_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MSD_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return MSD_OK;
+}
+
+msd_status valloc(msd_ctx* c, void** p, size_t bytes) {
+    unsigned char* q = nullptr;
+    msd_status s = dalloc(c, &q, bytes);
+    *p = q;
+    return s;
+}
+
+template <typename T>
+msd_status upload(msd_ctx* c, T** p, const T* src, size_t count) {
+    msd_status s = dalloc(c, p, count);
+    if (s != MSD_OK) return s;
+    if (count) {
+        cudaError_t e = cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+    return MSD_OK;
+}
+
+#define TRY(x)                              \
+    do {                                    \
+        msd_status _s = (x);                \
+        if (_s != MSD_OK) return _s;        \
+    } while (0)
+
+msd_status validate(const msd_problem* p) {
+    if (!p) return fail(nullptr, MSD_ERR_ARG, "problem is NULL");
+    if (p->n_walkers < 1) return fail(nullptr, MSD_ERR_ARG, "n_walkers must be >= 1");
+    if (p->refresh_K < 1) return fail(nullptr, MSD_ERR_ARG, "refresh_K must be >= 1");
+    if (p->prec != MSD_FP64 && p->prec != MSD_MIXED) return fail(nullptr, MSD_ERR_ARG, "unknown precision");
+    if (p->n_nuc < 1 || !p->nuc_xyz) return fail(nullptr, MSD_ERR_ARG, "need at least one nucleus");
+    if (p->n_basis < 1 || !p->bas_center || !p->bas_lm || !p->bas_alpha)
+        return fail(nullptr, MSD_ERR_ARG, "basis arrays missing");
+    for (int mu = 0; mu < p->n_basis; ++mu) {
+        if (p->bas_center[mu] < 0 || p->bas_center[mu] >= p->n_nuc)
+            return fail(nullptr, MSD_ERR_ARG, "bas_center[%d] out of range", mu);
+        if (p->bas_lm[mu] < 0 || p->bas_lm[mu] > 3) return fail(nullptr, MSD_ERR_ARG, "bas_lm[%d] not in 0..3", mu);
+        if (!(p->bas_alpha[mu] > 0.0) || !std::isfinite(p->bas_alpha[mu]))
+            return fail(nullptr, MSD_ERR_ARG, "bas_alpha[%d] must be positive and finite", mu);
+    }
+    for (int s = 0; s < 2; ++s) {
+        const int n = p->n_elec[s], N = p->n_orb[s];
+        if (n < 1 || n > MSD_MAX_ORB) return fail(nullptr, MSD_ERR_ARG, "n_elec[%d] = %d not in 1..%d", s, n, MSD_MAX_ORB);
+        if (N < n || N - n > MSD_MAX_ORB) return fail(nullptr, MSD_ERR_ARG, "n_orb[%d] = %d invalid", s, N);
+        if (!p->B[s]) return fail(nullptr, MSD_ERR_ARG, "B[%d] is NULL", s);
+        if (p->n_exc[s] < 1 || !p->exc_off[s]) return fail(nullptr, MSD_ERR_ARG, "n_exc[%d] must be >= 1", s);
+        const int32_t* off = p->exc_off[s];
+        if (off[0] != 0 || off[1] != 0) return fail(nullptr, MSD_ERR_ARG, "string 0 of spin %d must be the reference", s);
+        const int m = N - n;
+        for (int u = 0; u < p->n_exc[s]; ++u) {
+            const int k = off[u + 1] - off[u];
+            if (k < 0 || k > MSD_MAX_ORDER || k > n || k > m)
+                return fail(nullptr, MSD_ERR_ARG, "string %d of spin %d has invalid order %d", u, s, k);
+            if (k && (!p->exc_holes[s] || !p->exc_parts[s]))
+                return fail(nullptr, MSD_ERR_ARG, "hole/particle arrays of spin %d missing", s);
+            for (int q = 0; q < k; ++q) {
+                const int h = p->exc_holes[s][off[u] + q], pa = p->exc_parts[s][off[u] + q];
+                if (h >= n || pa >= m)
+                    return fail(nullptr, MSD_ERR_ARG, "string %d of spin %d: index out of range", u, s);
+                if (q && (h <= p->exc_holes[s][off[u] + q - 1] || pa <= p->exc_parts[s][off[u] + q - 1]))
+                    return fail(nullptr, MSD_ERR_ARG, "string %d of spin %d: indices not strictly ascending", u, s);
+            }
+        }
+    }
+    if (p->n_det < 1 || !p->det_up || !p->det_dn || !p->ci) return fail(nullptr, MSD_ERR_ARG, "term arrays missing");
+    if (p->n_det > (int64_t)0x7fffffff) return fail(nullptr, MSD_ERR_ARG, "n_det too large");
+    for (int64_t I = 0; I < p->n_det; ++I) {
+        if (p->det_up[I] < 0 || p->det_up[I] >= p->n_exc[0] || p->det_dn[I] < 0 || p->det_dn[I] >= p->n_exc[1])
+            return fail(nullptr, MSD_ERR_ARG, "term %lld refers to a missing string", (long long)I);
+        if (!std::isfinite(p->ci[I])) return fail(nullptr, MSD_ERR_ARG, "ci[%lld] not finite", (long long)I);
+    }
+    const bool mixed = p->prec == MSD_MIXED;
+    for (int s = 0; s < 2; ++s) {
+        const int n = p->n_elec[s], m = p->n_orb[s] - p->n_elec[s];
+        const size_t need = ratio_smem_bytes(mixed, n, m, NCH);
+        const size_t inv = (size_t)n * (n + 1) * 8 + (size_t)n * 12 + 16;
+        if (need > 220 * 1024 || inv > 220 * 1024)
+            return fail(nullptr, MSD_ERR_ARG,
+                        "spin %d: per-walker table (%d x %d) does not fit in one SM's shared memory", s, n, m);
+    }
+    return MSD_OK;
+}
+
+// Build device strings of spin s, grouped by order and sorted within each order.
+msd_status build_strings(msd_ctx* c, const msd_problem* p, int s) {
+    SpinConst& S = c->sp[s];
+    const int ne = p->n_exc[s];
+    const int32_t* off = p->exc_off[s];
+    std::vector<int> order(ne);
+    std::iota(order.begin(), order.end(), 0);
+    auto key_less = [&](int a, int b) {
+        const int ka = off[a + 1] - off[a], kb = off[b + 1] - off[b];
+        if (a == 0 || b == 0) return a == 0 && b != 0;  // the reference stays first
+        if (ka != kb) return ka < kb;
+        for (int q = 0; q < ka; ++q) {
+            const int ha = p->exc_holes[s][off[a] + q], hb = p->exc_holes[s][off[b] + q];
+            if (ha != hb) return ha < hb;
+        }
+        for (int q = 0; q < ka; ++q) {
+            const int pa = p->exc_parts[s][off[a] + q], pb = p->exc_parts[s][off[b] + q];
+            if (pa != pb) return pa < pb;
+        }
+        return a < b;
+    };
+    std::stable_sort(order.begin(), order.end(), key_less);
+    S.user_of = order;
+    S.internal_of.assign(ne, 0);
+    for (int i = 0; i < ne; ++i) S.internal_of[order[i]] = i;
+    S.hist.assign(MAXK + 1, 0);
+    S.g.n_exc = ne;
+    S.g.kmax = 0;
+    for (int k = 0; k <= MAXK + 1; ++k) S.g.goff[k] = 0;
+    std::vector<int> kof(ne);
+    for (int i = 0; i < ne; ++i) {
+        const int u = order[i];
+        kof[i] = off[u + 1] - off[u];
+        S.hist[kof[i]]++;
+        S.g.kmax = std::max(S.g.kmax, kof[i]);
+    }
+    // group boundaries: goff[k] = first internal index of order >= k
+    int acc = 0;
+    for (int k = 0; k <= MAXK; ++k) {
+        S.g.goff[k] = acc;
+        acc += (int)S.hist[k];
+    }
+    S.g.goff[MAXK + 1] = acc;
+    // records
+    std::vector<uint8_t> rec;
+    for (int k = 0; k <= MAXK + 1; ++k) S.g.roff[k] = 0;
+    for (int k = 1; k <= MAXK; ++k) {
+        while (rec.size() % 16) rec.push_back(0);
+        S.g.roff[k] = (long long)rec.size();
+        const int rb = rec_bytes(k);
+        for (int i = S.g.goff[k]; i < S.g.goff[k + 1]; ++i) {
+            const int u = order[i];
+            const size_t base = rec.size();
+            rec.resize(base + rb, 0);
+            for (int q = 0; q < k; ++q) {
+                rec[base + q] = p->exc_holes[s][off[u] + q];
+                rec[base + k + q] = p->exc_parts[s][off[u] + q];
+            }
+        }
+    }
+    while (rec.size() % 16) rec.push_back(0);
+    uint8_t* d_rec = nullptr;
+    TRY(upload(c, &d_rec, rec.data(), rec.size()));
+    S.g.rec = d_rec;
+    return MSD_OK;
+}
+
+// Terms grouped by the internal string of spin s (the moving spin), for C_s.
+msd_status build_terms(msd_ctx* c, const msd_problem* p, int s) {
+    SpinConst& S = c->sp[s];
+    const SpinConst& O = c->sp[1 - s];
+    const int ne = p->n_exc[s];
+    const int64_t nd = p->n_det;
+    const int32_t* mine = s == 0 ? p->det_up : p->det_dn;
+    const int32_t* oth = s == 0 ? p->det_dn : p->det_up;
+    std::vector<int> off(ne + 1, 0);
+    for (int64_t I = 0; I < nd; ++I) off[S.internal_of[mine[I]] + 1]++;
+    for (int u = 0; u < ne; ++u) off[u + 1] += off[u];
+    std::vector<int> pos(off.begin(), off.end() - 1);
+    std::vector<int> other(nd);
+    std::vector<double> cc(nd);
+    for (int64_t I = 0; I < nd; ++I) {
+        const int u = S.internal_of[mine[I]];
+        const int q = pos[u]++;
+        other[q] = O.internal_of[oth[I]];
+        cc[q] = p->ci[I];
+    }
+    std::vector<int> heavy;
+    for (int u = 0; u < ne; ++u)
+        if (off[u + 1] - off[u] > heavy_threshold()) heavy.push_back(u);
+    TRY(upload(c, &S.t_off, off.data(), off.size()));
+    TRY(upload(c, &S.t_other, other.data(), other.size()));
+    TRY(upload(c, &S.t_c, cc.data(), cc.size()));
+    S.n_heavy = (int)heavy.size();
+    TRY(upload(c, &S.heavy, heavy.data(), heavy.size()));
+    return MSD_OK;
+}
+
+msd_status alloc_state(msd_ctx* c, State& st) {
+    if (st.alloc) return MSD_OK;
+    const size_t W = c->W;
+    TRY(dalloc(c, &st.R, W * c->n_tot * 3));
+    TRY(dalloc(c, &st.S, W));
+    for (int s = 0; s < 2; ++s) {
+        const SpinConst& S = c->sp[s];
+        TRY(dalloc(c, &st.Ainv[s], W * S.n * S.n));
+        TRY(valloc(c, &st.T[s], W * S.n * std::max(S.m, 1) * c->tb));
+        TRY(dalloc(c, &st.logdet[s], W));
+        TRY(dalloc(c, &st.sgn[s], W));
+        TRY(valloc(c, &st.t[s], W * S.g.n_exc * c->tb));
+        TRY(valloc(c, &st.C[s], W * S.g.n_exc * c->tb));
+    }
+    st.alloc = true;
+    return MSD_OK;
+}
+
+// A7: recompute A_0^{-1}, log|det A_0| and T of spin s from the positions (Section III).
+msd_status refresh_spin(msd_ctx* c, State& st, int s) {
+    const SpinConst& S = c->sp[s];
+    launch_orbitals(c->L(), c->mixed, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas, c->blm, c->nb,
+                    S.B, S.N, c->Phi);
+    launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s]);
+    if (S.m > 0) launch_table(c->L(), c->mixed, c->W, S.n, S.N, st.Ainv[s], c->Phi, st.T[s]);
+    st.since_refresh[s] = 0;
+    st.C_valid[1 - s] = false;  // C of the other spin depends on this spin's t
+    return check_launch(c, "refresh");
+}
+
+// C_s from the current table of the other spin.
+msd_status ensure_C(msd_ctx* c, State& st, int s) {
+    if (st.C_valid[s]) return MSD_OK;
+    const SpinConst& S = c->sp[s];
+    const SpinConst& O = c->sp[1 - s];
+    launch_exc_det(c->L(), c->mixed, c->W, O.n, O.m, O.g, st.T[1 - s], st.t[1 - s]);
+    launch_ci_contract(c->L(), c->mixed, c->W, S.g.n_exc, O.g.n_exc, S.t_off, S.t_other, S.t_c, st.t[1 - s], st.C[s]);
+    launch_ci_contract_heavy(c->L(), c->mixed, c->W, S.g.n_exc, O.g.n_exc, S.n_heavy, S.heavy, S.t_off, S.t_other,
+                             S.t_c, st.t[1 - s], st.C[s]);
+    st.C_valid[s] = true;
+    return check_launch(c, "CI contraction");
+}
+
+// S = sum_u C_s[u] t_s[u] from the current table of spin s.
+msd_status recompute_S(msd_ctx* c, State& st, int s) {
+    const SpinConst& S = c->sp[s];
+    launch_exc_det(c->L(), c->mixed, c->W, S.n, S.m, S.g, st.T[s], st.t[s]);
+    launch_ci_dot(c->L(), c->mixed, c->W, S.g.n_exc, st.C[s], st.t[s], st.S);
+    return check_launch(c, "CI sum");
+}
+
+msd_status set_positions(msd_ctx* c, State& st, const double* R_dev) {
+    cudaError_t e = cudaMemcpyAsync(st.R, R_dev, sizeof(double) * c->W * c->n_tot * 3, cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of positions: %s", cudaGetErrorString(e));
+    TRY(refresh_spin(c, st, 0));
+    TRY(refresh_spin(c, st, 1));
+    st.C_valid[0] = st.C_valid[1] = false;
+    TRY(ensure_C(c, st, 0));
+    TRY(recompute_S(c, st, 0));
+    st.ready = true;
+    return MSD_OK;
+}
+
+int spin_of(const msd_ctx* c, int e) { return e < c->sp[0].n ? 0 : 1; }
+
+// Orbitals at the current position of electron e, then the bordered sweep with rnew = r_e.
+msd_status grad_lap_one(msd_ctx* c, State& st, int e, double* grad, long long gs, double* lap, long long ls) {
+    const int s = spin_of(c, e);
+    const SpinConst& S = c->sp[s];
+    TRY(ensure_C(c, st, s));
+    launch_orbitals(c->L(), c->mixed, NCH, c->W, 1, st.R, (long long)c->n_tot * 3, e, c->bas, c->blm, c->nb, S.B, S.N,
+                    c->phi_tmp);
+    RatioArgs a{};
+    a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = e - S.off; a.nch = NCH;
+    a.phi = c->phi_tmp; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
+    a.ratio = c->dummy; a.rs = 1; a.grad = grad; a.gs = gs; a.lap = lap; a.ls = ls;
+    if (S.m == 0) a.g.kmax = 0;
+    launch_ratio(c->L_sweep(), c->mixed, a);
+    return check_launch(c, "grad/lap");
+}
+
+}  // namespace
+
+extern "C" {
+
+msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
+    g_init_error.clear();
+    if (!out) return fail(nullptr, MSD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_systems != 1)
+        return fail(nullptr, MSD_ERR_ARG, "n_systems = %d: this build handles one system per context", n_systems);
+    TRY(validate(p));
+    msd_ctx* c = new msd_ctx();
+    c->W = p->n_walkers;
+    c->n_tot = p->n_elec[0] + p->n_elec[1];
+    c->nb = p->n_basis;
+    c->K = p->refresh_K;
+    c->mixed = p->prec == MSD_MIXED;
+    c->tb = c->mixed ? 4 : 8;
+    c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    auto bail = [&](msd_status s) {
+        g_init_error = c->err;
+        msd_destroy(c);
+        return s;
+    };
+    for (int s = 0; s < 2; ++s) {
+        c->sp[s].n = p->n_elec[s];
+        c->sp[s].N = p->n_orb[s];
+        c->sp[s].m = p->n_orb[s] - p->n_elec[s];
+        c->sp[s].off = s ? p->n_elec[0] : 0;
+    }
+    msd_status st;
+    // basis
+    std::vector<double4> bas(c->nb);
+    for (int mu = 0; mu < c->nb; ++mu) {
+        const double* A = p->nuc_xyz + 3 * p->bas_center[mu];
+        bas[mu] = make_double4(A[0], A[1], A[2], p->bas_alpha[mu]);
+    }
+    if ((st = upload(c, &c->bas, bas.data(), bas.size())) != MSD_OK) return bail(st);
+    if ((st = upload(c, &c->blm, p->bas_lm, (size_t)c->nb)) != MSD_OK) return bail(st);
+    for (int s = 0; s < 2; ++s) {
+        SpinConst& S = c->sp[s];
+        const size_t cnt = (size_t)c->nb * S.N;
+        if (c->mixed) {
+            std::vector<float> b32(p->B[s], p->B[s] + cnt);
+            float* d = nullptr;
+            if ((st = upload(c, &d, b32.data(), cnt)) != MSD_OK) return bail(st);
+            S.B = d;
+        } else {
+            double* d = nullptr;
+            if ((st = upload(c, &d, p->B[s], cnt)) != MSD_OK) return bail(st);
+            S.B = d;
+        }
+        if ((st = build_strings(c, p, s)) != MSD_OK) return bail(st);
+    }
+    for (int s = 0; s < 2; ++s)
+        if ((st = build_terms(c, p, s)) != MSD_OK) return bail(st);
+    const int nmax = std::max(c->sp[0].n, c->sp[1].n);
+    const int Nmax = std::max(c->sp[0].N, c->sp[1].N);
+    const int mmax = std::max(std::max(c->sp[0].m, c->sp[1].m), 1);
+    const size_t W = c->W;
+    if ((st = valloc(c, &c->Phi, W * nmax * Nmax * c->tb)) != MSD_OK) return bail(st);
+    if ((st = valloc(c, &c->phi_new, W * NCH * Nmax * c->tb)) != MSD_OK) return bail(st);
+    if ((st = valloc(c, &c->phi_tmp, W * NCH * Nmax * c->tb)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->rho, W)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->num, W * NCH)) != MSD_OK) return bail(st);
+    if ((st = valloc(c, &c->y0, W * mmax * c->tb)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->rnew, W * 3)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->dummy, W)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_io, W * 8)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_acc, W)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_status, 1)) != MSD_OK) return bail(st);
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(c, MSD_ERR_CUDA, "memset"));
+    if ((st = alloc_state(c, c->st)) != MSD_OK) return bail(st);
+    *out = c;
+    return MSD_OK;
+}
+
+msd_status msd_set_positions(msd_ctx* c, const double* R_dev) {
+    if (!c || !R_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    c->prop_valid = false;
+    return set_positions(c, c->st, R_dev);
+}
+
+msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
+                     double* lap_dev) {
+    if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if ((grad_dev == nullptr) != (lap_dev == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    State& st = c->st;
+    const int s = spin_of(c, elec);
+    const SpinConst& S = c->sp[s];
+    if (st.since_refresh[s] >= c->K) {
+        TRY(refresh_spin(c, st, s));
+        TRY(ensure_C(c, st, s));
+        TRY(recompute_S(c, st, s));
+    } else {
+        TRY(ensure_C(c, st, s));
+    }
+    st.since_refresh[s]++;
+    const int nch = grad_dev ? NCH : 1;
+    cudaError_t e = cudaMemcpyAsync(c->rnew, rnew_dev, sizeof(double) * c->W * 3, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
+    launch_orbitals(c->L(), c->mixed, nch, c->W, 1, c->rnew, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, c->phi_new);
+    RatioArgs a{};
+    a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = elec - S.off; a.nch = nch;
+    a.phi = c->phi_new; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
+    a.ratio = ratio_dev; a.rs = 1; a.grad = grad_dev; a.gs = 3; a.lap = lap_dev; a.ls = 1;
+    a.rho = c->rho; a.num = c->num; a.y0 = c->y0;
+    if (S.m == 0) a.g.kmax = 0;
+    launch_ratio(c->L_sweep(), c->mixed, a);
+    TRY(check_launch(c, "ratio"));
+    c->prop_elec = elec;
+    c->prop_nch = nch;
+    c->prop_valid = true;
+    return MSD_OK;
+}
+
+msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
+    if (!c || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (!c->prop_valid || c->prop_elec != elec)
+        return fail(c, MSD_ERR_STATE, "msd_accept(%d) without a matching msd_ratio proposal", elec);
+    State& st = c->st;
+    const int s = spin_of(c, elec);
+    const SpinConst& S = c->sp[s];
+    AcceptArgs a{};
+    a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = elec - S.off; a.elec = elec; a.n_tot = c->n_tot;
+    a.accept = accept_dev; a.phi = c->phi_new; a.nch = c->prop_nch; a.rho = c->rho; a.num = c->num; a.y0 = c->y0;
+    a.rnew = c->rnew; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.R = st.R; a.logdet = st.logdet[s]; a.sgn = st.sgn[s];
+    a.S = st.S;
+    launch_accept(c->L(), c->mixed, a);
+    st.C_valid[1 - s] = false;
+    c->prop_valid = false;
+    return check_launch(c, "accept");
+}
+
+msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev) {
+    if (!c || !grad_dev || !lap_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < -1 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    if (elec >= 0) return grad_lap_one(c, c->st, elec, grad_dev, 3, lap_dev, 1);
+    for (int e = 0; e < c->n_tot; ++e)
+        TRY(grad_lap_one(c, c->st, e, grad_dev + 3 * e, 3LL * c->n_tot, lap_dev + e, c->n_tot));
+    return MSD_OK;
+}
+
+msd_status msd_eval_batch(msd_ctx* c, const double* R_dev, double* logabs_dev, double* sign_dev, double* grad_dev,
+                          double* lap_dev) {
+    if (!c || !R_dev || !logabs_dev || !sign_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if ((grad_dev == nullptr) != (lap_dev == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
+    TRY(alloc_state(c, c->scratch));
+    State& st = c->scratch;
+    TRY(set_positions(c, st, R_dev));
+    launch_state(c->L(), c->W, st.logdet[0], st.sgn[0], st.logdet[1], st.sgn[1], st.S, logabs_dev, sign_dev);
+    if (grad_dev)
+        for (int e = 0; e < c->n_tot; ++e)
+            TRY(grad_lap_one(c, st, e, grad_dev + 3 * e, 3LL * c->n_tot, lap_dev + e, c->n_tot));
+    return check_launch(c, "eval_batch");
+}
+
+msd_status msd_get_state(msd_ctx* c, double* R_dev, double* logabs_dev, double* sign_dev) {
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    State& st = c->st;
+    if (R_dev) {
+        cudaError_t e = cudaMemcpyAsync(R_dev, st.R, sizeof(double) * c->W * c->n_tot * 3, cudaMemcpyDeviceToDevice,
+                                        c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of positions: %s", cudaGetErrorString(e));
+    }
+    if (logabs_dev || sign_dev)
+        launch_state(c->L(), c->W, st.logdet[0], st.sgn[0], st.logdet[1], st.sgn[1], st.S, logabs_dev, sign_dev);
+    return check_launch(c, "get_state");
+}
+
+msd_status msd_propose(msd_ctx* c, int32_t elec, const double* eta_dev, double tau, double* rnew_dev) {
+    if (!c || !eta_dev || !rnew_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    launch_propose(c->L(), c->W, c->n_tot, elec, c->st.R, eta_dev, tau, rnew_dev);
+    return check_launch(c, "propose");
+}
+
+msd_status msd_metropolis(msd_ctx* c, const double* u_dev, const double* ratio_dev, uint8_t* accept_dev) {
+    if (!c || !u_dev || !ratio_dev || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    launch_metropolis(c->L(), c->W, u_dev, ratio_dev, accept_dev);
+    return check_launch(c, "metropolis");
+}
+
+msd_status msd_ratio_host(msd_ctx* c, int32_t elec, const double* rnew_host, double* ratio_host, double* grad_host,
+                          double* lap_host) {
+    if (!c || !rnew_host || !ratio_host) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if ((grad_host == nullptr) != (lap_host == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_host and lap_host must be both NULL or both set");
+    const size_t W = c->W;
+    double* d_rnew = c->d_io;          // [W][3]
+    double* d_ratio = c->d_io + 3 * W; // [W]
+    double* d_grad = c->d_io + 4 * W;  // [W][3]
+    double* d_lap = c->d_io + 7 * W;   // [W]
+    cudaError_t e = cudaMemcpyAsync(d_rnew, rnew_host, sizeof(double) * 3 * W, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    TRY(msd_ratio(c, elec, d_rnew, d_ratio, grad_host ? d_grad : nullptr, grad_host ? d_lap : nullptr));
+    e = cudaMemcpyAsync(ratio_host, d_ratio, sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && grad_host) {
+        e = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * 3 * W, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lap_host, d_lap, sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "download: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+msd_status msd_accept_host(msd_ctx* c, int32_t elec, const uint8_t* accept_host) {
+    if (!c || !accept_host) return fail(c, MSD_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpyAsync(c->d_acc, accept_host, c->W, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    TRY(msd_accept(c, elec, c->d_acc));
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "sync: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+msd_status msd_set_stream(msd_ctx* c, void* stream) {
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    c->stream = static_cast<cudaStream_t>(stream);
+    return MSD_OK;
+}
+
+msd_status msd_sync(msd_ctx* c) {
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    int status = 0;
+    e = cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "status read: %s", cudaGetErrorString(e));
+    if (status) {
+        cudaMemset(c->d_status, 0, sizeof(int));
+        if (status & ST_SINGULAR) return fail(c, MSD_ERR_SINGULAR, "a reference determinant or ratio was zero");
+        return fail(c, MSD_ERR_SINGULAR, "a ratio was not finite");
+    }
+    return MSD_OK;
+}
+
+const char* msd_last_error(const msd_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+msd_status msd_exc_histogram(const msd_ctx* c, int32_t spin, int64_t* out) {
+    if (!c || !out || spin < 0 || spin > 1) return MSD_ERR_ARG;
+    out[0] = c->sp[spin].g.n_exc;
+    for (int k = 0; k <= MAXK; ++k) out[1 + k] = c->sp[spin].hist[k];
+    return MSD_OK;
+}
+
+msd_status msd_copy_state(msd_ctx* c, int32_t item, int32_t spin, void* dst, int64_t* bytes) {
+    if (!c || spin < 0 || spin > 1 || item < 0 || item > 11) return fail(c, MSD_ERR_ARG, "invalid argument");
+    if (item >= 8) {
+        if (c->prop_elec < 0) return fail(c, MSD_ERR_STATE, "no msd_ratio proposal yet");
+        spin = c->prop_elec < c->sp[0].n ? 0 : 1;
+    }
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    const State& st = c->st;
+    const SpinConst& S = c->sp[spin];
+    const size_t W = c->W;
+    const void* src = nullptr;
+    size_t nb = 0;
+    switch (item) {
+        case 0: src = st.R; nb = W * c->n_tot * 3 * 8; break;
+        case 1: src = st.Ainv[spin]; nb = W * S.n * S.n * 8; break;
+        case 2: src = st.T[spin]; nb = W * S.n * S.m * c->tb; break;
+        case 3: src = st.logdet[spin]; nb = W * 8; break;
+        case 4: src = st.sgn[spin]; nb = W * 8; break;
+        case 5: src = st.S; nb = W * 8; break;
+        case 6: src = st.C[spin]; nb = W * S.g.n_exc * c->tb; break;
+        case 7: src = st.t[spin]; nb = W * S.g.n_exc * c->tb; break;
+        case 8: src = c->rho; nb = W * 8; break;
+        case 9: src = c->num; nb = W * NCH * 8; break;
+        case 10: src = c->y0; nb = W * S.m * c->tb; break;
+        case 11: src = c->phi_new; nb = W * c->prop_nch * S.N * c->tb; break;
+    }
+    if (bytes) *bytes = (int64_t)nb;
+    if (dst && nb) {
+        cudaError_t e = cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    }
+    return MSD_OK;
+}
+
+msd_status msd_timing_start(msd_ctx* c) {
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    c->timing = true;
+    c->launches = 0;
+    c->ev_used = 0;
+    return MSD_OK;
+}
+
+msd_status msd_timing_stop(msd_ctx* c, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches) {
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "event time: %s", cudaGetErrorString(e));
+        tot += ms;
+    }
+    if (sweep_ms) *sweep_ms = tot;
+    if (sweep_launches) *sweep_launches = (int64_t)(c->ev_used / 2);
+    if (all_launches) *all_launches = c->launches;
+    c->timing = false;
+    c->ev_used = 0;
+    return MSD_OK;
+}
+
+void msd_destroy(msd_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+}  // extern "C"

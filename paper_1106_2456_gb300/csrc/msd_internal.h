@@ -1,0 +1,122 @@
+// msd_internal.h -- shared declarations of the libmsd CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "msd.h"
+
+namespace msd {
+
+constexpr int MAXK = MSD_MAX_ORDER;
+constexpr int NCH = 5;  // channels: value, d/dx, d/dy, d/dz, laplacian
+
+enum StatusBits : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
+
+// Bytes of one excitation record of order k: k hole bytes, k particle bytes, padded to a
+// power of two so one vector load fetches it.
+__host__ __device__ constexpr int rec_bytes(int k) {
+    return k <= 1 ? 2 : k == 2 ? 4 : k <= 4 ? 8 : 16;
+}
+
+// Excitation strings of one spin on the device, grouped by order.  Internal index i of
+// order k lies in [goff[k], goff[k+1]); group 0 holds the reference.  Group k's records
+// start at byte roff[k] of rec.  Within a group strings are sorted lexicographically by
+// (holes, particles) so consecutive threads share table rows.
+struct ExcDev {
+    int n_exc = 0;
+    int kmax = 0;
+    int goff[MAXK + 2] = {0};
+    long long roff[MAXK + 2] = {0};
+    const uint8_t* rec = nullptr;
+};
+
+// Kernel launch wrappers (msd_kernels.cu).  Template parameter pairs are selected at
+// run time by `mixed`: FP64 everywhere, or FP32 orbitals/table/excitations.
+struct Launch {
+    cudaStream_t stream;
+    int* status;             // device status word
+    long long* launches;     // host counter of kernel launches (nullable)
+    cudaEvent_t t0 = nullptr;  // recorded before/after the excitation-sweep kernel (nullable)
+    cudaEvent_t t1 = nullptr;
+    void count(int k = 1) const {
+        if (launches) *launches += k;
+    }
+};
+
+// Orbitals phi^a_j at P points.  Point p belongs to walker p / ppw and sits at
+// pos + (p / ppw) * wstride + (p_off + p % ppw) * 3.  out[p][a][j], a < nch (1 or 5).
+void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const double* pos,
+                     long long wstride, int p_off, const double4* bas, const int8_t* blm, int nb,
+                     const void* B, int N, void* out);
+
+// Gauss-Jordan inverse with partial pivoting of A_0 = Phi[w][:, :n] for every walker.
+void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv,
+                    double* logdet, double* sgn);
+
+// T[w] = Ainv[w] * Phi[w][:, n:N].
+void launch_table(const Launch& L, bool mixed, int W, int n, int N, const double* Ainv, const void* Phi,
+                  void* T);
+
+// t[w][i] = det T_i (value of every excitation ratio, Section III).
+void launch_exc_det(const Launch& L, bool mixed, int W, int n, int m, const ExcDev& g, const void* T, void* t);
+
+// C[w][u] = sum_{I in terms(u)} c_I t_other[w][other_I].  The light kernel skips strings with
+// more than heavy_threshold() terms; the heavy kernel reduces those with a block each.
+void launch_ci_contract(const Launch& L, bool mixed, int W, int n_exc, int n_exc_other, const int* off,
+                        const int* other, const double* c, const void* t_other, void* C);
+void launch_ci_contract_heavy(const Launch& L, bool mixed, int W, int n_exc, int n_exc_other, int n_heavy,
+                              const int* heavy, const int* off, const int* other, const double* c,
+                              const void* t_other, void* C);
+int heavy_threshold();
+
+// S[w] = sum_u C[w][u] t[w][u] in FP64.
+void launch_ci_dot(const Launch& L, bool mixed, int W, int n_exc, const void* C, const void* t, double* S);
+
+struct RatioArgs {
+    int W, n, N, m, row, nch;
+    const void* phi;       // [W][nch][N] orbitals at the evaluated position
+    const double* Ainv;    // [W][n][n]
+    const void* T;         // [W][n][m]
+    const void* C;         // [W][n_exc]
+    const double* S;       // [W]
+    ExcDev g;
+    double* ratio; long long rs;   // ratio[w * rs]
+    double* grad; long long gs;    // grad[w * gs + a]
+    double* lap; long long ls;     // lap[w * ls]
+    double* rho;           // [W] saved proposal (nullable)
+    double* num;           // [W][NCH] saved proposal (nullable)
+    void* y0;              // [W][m] saved proposal (nullable)
+};
+void launch_ratio(const Launch& L, bool mixed, const RatioArgs& a);
+
+struct AcceptArgs {
+    int W, n, N, m, row, elec, n_tot;
+    const uint8_t* accept;
+    const void* phi;       // [W][nch][N], channel 0 = values at r'
+    int nch;
+    const double* rho;
+    const double* num;     // [W][NCH]
+    const void* y0;        // [W][m]
+    const double* rnew;    // [W][3]
+    double* Ainv;
+    void* T;
+    double* R;
+    double* logdet;
+    double* sgn;
+    double* S;
+};
+void launch_accept(const Launch& L, bool mixed, const AcceptArgs& a);
+
+void launch_propose(const Launch& L, int W, int n_tot, int elec, const double* R, const double* eta, double tau,
+                    double* rnew);
+void launch_metropolis(const Launch& L, int W, const double* u, const double* ratio, uint8_t* accept);
+void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, const double* ld1,
+                  const double* sg1, const double* S, double* logabs, double* sign);
+
+size_t ratio_smem_bytes(bool mixed, int n, int m, int nch);
+
+}  // namespace msd

@@ -1,0 +1,868 @@
+// msd_kernels.cu -- CUDA kernels of the multi-determinant table method for sm_103a.
+//
+// Notation (per spin): n electrons, N orbitals, m = N - n virtuals.
+//   A_0[r][c] = phi_c(r_r)            reference Slater matrix   (Section II, M(i,j) = phi_j(r_i))
+//   Ainv[c][r] = (A_0^{-1})[c][r]     stored row-major per walker
+//   T[c][a] = sum_r Ainv[c][r] phi_{n+a}(r_r)   excitation table (Section III, Algorithm 1 step 3)
+// An excitation u of order k (holes h_q, particles p_l) has det A_u / det A_0 = det T_u with
+// T_u[q][l] = T[h_q][p_l] (Section III).  Moving electron i to r' gives (Sherman-Morrison,
+// Section III) x = Ainv[:, i], rho = phi_occ(r') . x, y = phi_virt(r') - T^T phi_occ(r') and
+//   det A_u(R') / det A_0(R) = det [[T_u, x_u], [-y_u^T, rho]]           (bordered form)
+// and the same with every phi(r') replaced by d^a phi(r') for the gradient and laplacian
+// channels (Section IV-A: the table with the electron's row replaced by derivative rows; the
+// bordered determinant is the generalised matrix determinant lemma of Section IV-C).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "msd_internal.h"
+#include "msd_smalldet.cuh"
+
+namespace msd {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ float texp(float x) { return expf(x); }
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV values over the block; every thread receives the totals.  red holds 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[warp * NV + i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < nw; ++q) s += red[q * NV + i];
+        v[i] = s;
+    }
+}
+
+__device__ __forceinline__ unsigned char* align16(void* p) {
+    uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    return reinterpret_cast<unsigned char*>((a + 15) & ~uintptr_t(15));
+}
+
+// Copy `count` elements global -> shared, 16-byte vectors when both ends allow it.
+template <typename TT>
+__device__ __forceinline__ void copy_to_smem(TT* dst, const TT* __restrict__ src, long long count) {
+    const long long bytes = count * (long long)sizeof(TT);
+    if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0 && (bytes & 15) == 0) {
+        const long long nv = bytes >> 4;
+        const uint4* s = reinterpret_cast<const uint4*>(src);
+        uint4* d = reinterpret_cast<uint4*>(dst);
+        for (long long i = threadIdx.x; i < nv; i += blockDim.x) d[i] = __ldg(s + i);
+    } else {
+        for (long long i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A1: basis functions and orbitals at a set of points
+// ------------------------------------------------------------------------------------------
+// chi_mu(r) = (r - A)_c^l exp(-alpha |r - A|^2) with its gradient and laplacian, then
+// phi^a_j = sum_mu chi^a_mu B[mu][j] (Algorithm 1 step 2).  PB points per block; phase 1
+// fills chi in shared memory, phase 2 streams B once per block and contracts.
+template <typename TO, int NC, int PB>
+__global__ void __launch_bounds__(128) k_orbitals(int P, int ppw, const double* __restrict__ pos,
+                                                  long long wstride, int p_off, const double4* __restrict__ bas,
+                                                  const int8_t* __restrict__ blm, int nb,
+                                                  const TO* __restrict__ B, int N, TO* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TO* chi = reinterpret_cast<TO*>(smem);  // [nb][PB * NC]
+    const int p0 = blockIdx.x * PB;
+    for (int idx = threadIdx.x; idx < PB * nb; idx += blockDim.x) {
+        const int q = idx / nb, mu = idx - q * nb;
+        const int p = p0 + q;
+        TO v[5] = {TO(0), TO(0), TO(0), TO(0), TO(0)};
+        if (p < P) {
+            const int w = p / ppw, r = p - w * ppw;
+            const double* rp = pos + (long long)w * wstride + (long long)(p_off + r) * 3;
+            const double4 b = bas[mu];
+            const TO d[3] = {TO(rp[0] - b.x), TO(rp[1] - b.y), TO(rp[2] - b.z)};
+            const TO al = TO(b.w);
+            const TO d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const TO g = texp(-al * d2);
+            const int lm = blm[mu];
+            if (lm == 0) {
+                v[0] = g;
+                v[1] = TO(-2) * al * d[0] * g;
+                v[2] = TO(-2) * al * d[1] * g;
+                v[3] = TO(-2) * al * d[2] * g;
+                v[4] = (TO(4) * al * al * d2 - TO(6) * al) * g;
+            } else {
+                const int c = lm - 1;
+                const TO dc = d[c];
+                v[0] = dc * g;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[1 + a] = ((a == c ? TO(1) : TO(0)) - TO(2) * al * d[a] * dc) * g;
+                v[4] = dc * (TO(4) * al * al * d2 - TO(10) * al) * g;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a) chi[mu * (PB * NC) + q * NC + a] = v[a];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        TO acc[PB * NC];
+#pragma unroll
+        for (int q = 0; q < PB * NC; ++q) acc[q] = TO(0);
+        for (int mu = 0; mu < nb; ++mu) {
+            const TO bj = __ldg(B + (long long)mu * N + j);
+            const TO* cr = chi + mu * (PB * NC);
+#pragma unroll
+            for (int q = 0; q < PB * NC; ++q) acc[q] = fma(cr[q], bj, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int p = p0 + q;
+            if (p < P)
+#pragma unroll
+                for (int a = 0; a < NC; ++a) out[((long long)p * NC + a) * N + j] = acc[q * NC + a];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A7: from-scratch inverse of A_0 (Gauss-Jordan with partial pivoting, FP64, one block per walker)
+// ------------------------------------------------------------------------------------------
+template <typename TO>
+__global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __restrict__ Phi,
+                                                    double* __restrict__ Ainv, double* __restrict__ logdet,
+                                                    double* __restrict__ sgn, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ld = n + 1;
+    double* a = reinterpret_cast<double*>(smem);  // [n][ld]
+    double* f = a + (long long)n * ld;            // [n]
+    int* piv = reinterpret_cast<int*>(f + n);     // [n]
+    __shared__ int s_p, s_bad;
+    __shared__ double s_logdet, s_sign, s_amax[32];
+    const int w = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int tx = tid & 31, ty = tid >> 5, ny = bd >> 5;
+    const TO* src = Phi + (long long)w * n * N;
+    // Eliminate on B = A_0^T: row operations on B give X with X B = I up to rounding, so
+    // A_0 X^T = I has a small residual -- the identity phi_occ(r_i)^T A_0^{-1} = e_i^T that the
+    // Sherman-Morrison row update and the table update rely on.
+    double amax = 0.0;
+    for (int c = ty; c < n; c += ny)
+        for (int r = tx; r < n; r += 32) {
+            const double v = double(src[(long long)r * N + c]);
+            a[c * ld + r] = v;  // a = A_0^T
+            amax = fmax(amax, fabs(v));
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (tx == 0) s_amax[ty] = amax;
+    if (tid == 0) {
+        s_logdet = 0.0;
+        s_sign = 1.0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    amax = 0.0;
+    for (int q = 0; q < ny; ++q) amax = fmax(amax, s_amax[q]);
+    // a pivot below n * 8 eps * max|A_0| means A_0 is singular to working precision
+    // (e.g. two electrons of one spin at the same point)
+    const double tiny = double(n) * 8.0 * 2.220446049250313e-16 * amax;
+    for (int k = 0; k < n; ++k) {
+        if (ty == 0) {
+            double best = -1.0;
+            int bi = k;
+            for (int r = k + tx; r < n; r += 32) {
+                const double v = fabs(a[r * ld + k]);
+                if (v > best) { best = v; bi = r; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tx == 0) { s_p = bi; piv[k] = bi; }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < n; j += bd) {
+                const double t = a[k * ld + j];
+                a[k * ld + j] = a[p * ld + j];
+                a[p * ld + j] = t;
+            }
+        __syncthreads();
+        const double pv = a[k * ld + k];
+        const bool bad = !(fabs(pv) > tiny) || !isfinite(pv);
+        const double ip = bad ? 0.0 : 1.0 / pv;
+        if (tid == 0) {
+            if (bad) s_bad = 1;
+            else {
+                s_logdet += log(fabs(pv));
+                if ((pv < 0.0) != (p != k)) s_sign = -s_sign;
+            }
+        }
+        for (int r = tid; r < n; r += bd) f[r] = a[r * ld + k];
+        __syncthreads();
+        for (int j = tid; j < n; j += bd) a[k * ld + j] = (j == k) ? ip : a[k * ld + j] * ip;
+        __syncthreads();
+        for (int r = ty; r < n; r += ny) {
+            if (r == k) continue;
+            const double fr = f[r];
+            for (int j = tx; j < n; j += 32) {
+                if (j == k) a[r * ld + k] = -fr * ip;
+                else a[r * ld + j] = fma(-fr, a[k * ld + j], a[r * ld + j]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k)
+            for (int r = tid; r < n; r += bd) {
+                const double t = a[r * ld + k];
+                a[r * ld + k] = a[r * ld + p];
+                a[r * ld + p] = t;
+            }
+        __syncthreads();
+    }
+    // a now holds (A_0^T)^{-1} = (A_0^{-1})^T; store A_0^{-1}[c][r] = a[r][c]
+    double* dst = Ainv + (long long)w * n * n;
+    for (int c = ty; c < n; c += ny)
+        for (int r = tx; r < n; r += 32) dst[c * n + r] = a[r * ld + c];
+    if (tid == 0) {
+        logdet[w] = s_bad ? -INFINITY : s_logdet;
+        sgn[w] = s_bad ? 0.0 : s_sign;
+        if (s_bad) atomicOr(status, ST_SINGULAR);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A7: excitation table T = A_0^{-1} Phi_virt (Algorithm 1 step 3: one matrix product)
+// ------------------------------------------------------------------------------------------
+// grid (ceil(m / 64), W); each thread owns a 4 x 4 register tile of a 64-column slab.
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBlock) k_table(int n, int N, const double* __restrict__ Ainv,
+                                                  const TO* __restrict__ Phi, TT* __restrict__ T) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = N - n, a0 = blockIdx.x * 64, w = blockIdx.y;
+    const int lda = n + 1;
+    TT* As = reinterpret_cast<TT*>(smem);                                  // [n][lda] = Ainv[c][r]
+    TT* Bs = reinterpret_cast<TT*>(align16(As + (long long)n * lda));       // [n][64] = Phi[r][n + a0 + a]
+    const double* Aw = Ainv + (long long)w * n * n;
+    const TO* Pw = Phi + (long long)w * n * N;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c = idx / n, r = idx - c * n;
+        As[c * lda + r] = TT(Aw[idx]);
+    }
+    for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
+        const int r = idx >> 6, a = idx & 63;
+        Bs[idx] = (a0 + a < m) ? TT(Pw[(long long)r * N + n + a0 + a]) : TT(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    TT* Tw = T + (long long)w * n * m;
+    for (int c0 = ty * 4; c0 < n; c0 += 64) {
+        TT acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = TT(0);
+        for (int r = 0; r < n; ++r) {
+            TT av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = (c0 + i < n) ? As[(c0 + i) * lda + r] : TT(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[r * 64 + tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i;
+            if (c >= n) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int a = a0 + tx * 4 + j;
+                if (a < m) Tw[(long long)c * m + a] = acc[i][j];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// excitation records and small determinants (Section III: r x r determinants of T entries)
+// ------------------------------------------------------------------------------------------
+// Raw record of order K as one vector load, and its decoding into hole/particle indices.
+template <int K>
+struct RecRaw {
+    using type = typename std::conditional<K == 1, unsigned short,
+                 typename std::conditional<K == 2, unsigned,
+                 typename std::conditional<(K <= 4), uint2, uint4>::type>::type>::type;
+};
+
+template <int K>
+__device__ __forceinline__ typename RecRaw<K>::type load_raw(const uint8_t* __restrict__ base, int i) {
+    return __ldg(reinterpret_cast<const typename RecRaw<K>::type*>(base) + i);
+}
+
+template <int K>
+__device__ __forceinline__ void decode_rec(const typename RecRaw<K>::type& v, int (&h)[K], int (&p)[K]) {
+    if constexpr (K == 1) {
+        h[0] = v & 0xff;
+        p[0] = (v >> 8) & 0xff;
+    } else if constexpr (K == 2) {
+        h[0] = v & 0xff;
+        h[1] = (v >> 8) & 0xff;
+        p[0] = (v >> 16) & 0xff;
+        p[1] = (v >> 24) & 0xff;
+    } else if constexpr (K <= 4) {
+        const unsigned wd[2] = {v.x, v.y};
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            h[q] = (wd[q >> 2] >> ((q & 3) * 8)) & 0xff;
+            p[q] = (wd[(K + q) >> 2] >> (((K + q) & 3) * 8)) & 0xff;
+        }
+    } else {
+        const unsigned wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            h[q] = (wd[q >> 2] >> ((q & 3) * 8)) & 0xff;
+            p[q] = (wd[(K + q) >> 2] >> (((K + q) & 3) * 8)) & 0xff;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void load_rec(const uint8_t* __restrict__ base, int i, int (&h)[K], int (&p)[K]) {
+    if constexpr (K == 1) {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+        h[0] = v & 0xff;
+        p[0] = (v >> 8) & 0xff;
+    } else if constexpr (K == 2) {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned*>(base) + i);
+        h[0] = v & 0xff;
+        h[1] = (v >> 8) & 0xff;
+        p[0] = (v >> 16) & 0xff;
+        p[1] = (v >> 24) & 0xff;
+    } else if constexpr (K <= 4) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(base) + i);
+        const unsigned wd[2] = {v.x, v.y};
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            h[q] = (wd[q >> 2] >> ((q & 3) * 8)) & 0xff;
+            p[q] = (wd[(K + q) >> 2] >> (((K + q) & 3) * 8)) & 0xff;
+        }
+    } else {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + i);
+        const unsigned wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            h[q] = (wd[q >> 2] >> ((q & 3) * 8)) & 0xff;
+            p[q] = (wd[(K + q) >> 2] >> (((K + q) & 3) * 8)) & 0xff;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// excitation values t_u = det T_u for every string (used for the CI sums at set-up/refresh)
+// ------------------------------------------------------------------------------------------
+template <int K, typename TT>
+__device__ __forceinline__ void det_group(const ExcDev& g, const TT* Ts, int ld, TT* tw) {
+    const int j0 = g.goff[K], j1 = g.goff[K + 1];
+    const uint8_t* rec = g.rec + g.roff[K];
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        int h[K], p[K];
+        load_rec<K>(rec, j - j0, h, p);
+        tw[j] = small_det<K, TT>(Ts, ld, h, p);
+    }
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(kBlock) k_exc_det(int n, int m, ExcDev g, const TT* __restrict__ T,
+                                                    TT* __restrict__ t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TT* Ts = reinterpret_cast<TT*>(smem);
+    const int w = blockIdx.x;
+    copy_to_smem(Ts, T + (long long)w * n * m, (long long)n * m);
+    __syncthreads();
+    TT* tw = t + (long long)w * g.n_exc;
+    for (int j = g.goff[0] + threadIdx.x; j < g.goff[1]; j += blockDim.x) tw[j] = TT(1);
+    for (int k = 1; k <= g.kmax; ++k) {
+        switch (k) {
+            case 1: det_group<1, TT>(g, Ts, m, tw); break;
+            case 2: det_group<2, TT>(g, Ts, m, tw); break;
+            case 3: det_group<3, TT>(g, Ts, m, tw); break;
+            case 4: det_group<4, TT>(g, Ts, m, tw); break;
+            case 5: det_group<5, TT>(g, Ts, m, tw); break;
+            case 6: det_group<6, TT>(g, Ts, m, tw); break;
+            case 7: det_group<7, TT>(g, Ts, m, tw); break;
+            case 8: det_group<8, TT>(g, Ts, m, tw); break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A5 preparation: C_s[u] = sum_{I : s-string of I is u} c_I t_other[other string of I]
+// ------------------------------------------------------------------------------------------
+template <typename TT>
+__global__ void __launch_bounds__(kBlock) k_ci_contract_light(int n_exc, int n_exc_other, const int* __restrict__ off,
+                                                              const int* __restrict__ other,
+                                                              const double* __restrict__ c,
+                                                              const TT* __restrict__ t_other, TT* __restrict__ C,
+                                                              int heavy_len) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.y;
+    if (u >= n_exc) return;
+    const int b = off[u], e = off[u + 1];
+    if (e - b > heavy_len) return;  // handled by k_ci_contract_heavy
+    const TT* tw = t_other + (long long)w * n_exc_other;
+    double acc = 0.0;
+    for (int q = b; q < e; ++q) acc = fma(__ldg(c + q), double(tw[__ldg(other + q)]), acc);
+    C[(long long)w * n_exc + u] = TT(acc);
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(kBlock) k_ci_contract_heavy(int n_exc, int n_exc_other, const int* __restrict__ heavy,
+                                                              const int* __restrict__ off,
+                                                              const int* __restrict__ other,
+                                                              const double* __restrict__ c,
+                                                              const TT* __restrict__ t_other, TT* __restrict__ C) {
+    __shared__ double red[32];
+    const int u = heavy[blockIdx.x];
+    const int w = blockIdx.y;
+    const TT* tw = t_other + (long long)w * n_exc_other;
+    double v[1] = {0.0};
+    for (int q = off[u] + threadIdx.x; q < off[u + 1]; q += blockDim.x)
+        v[0] = fma(__ldg(c + q), double(tw[__ldg(other + q)]), v[0]);
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) C[(long long)w * n_exc + u] = TT(v[0]);
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(kBlock) k_ci_dot(int n_exc, const TT* __restrict__ C, const TT* __restrict__ t,
+                                                   double* __restrict__ S) {
+    __shared__ double red[32];
+    const int w = blockIdx.x;
+    const TT* Cw = C + (long long)w * n_exc;
+    const TT* tw = t + (long long)w * n_exc;
+    double v[1] = {0.0};
+    for (int u = threadIdx.x; u < n_exc; u += blockDim.x) v[0] = fma(double(Cw[u]), double(tw[u]), v[0]);
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) S[w] = v[0];
+}
+
+// ------------------------------------------------------------------------------------------
+// A2-A5: reference ratio, virtual-row contraction, excitation sweep and CI reduction
+// ------------------------------------------------------------------------------------------
+template <int K, int NC, typename TT>
+__device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int ld, const TT* xs, const TT* ys,
+                                            int ldy, const TT (&s)[NC], const TT* __restrict__ Cw,
+                                            Accum<TT, NC>& acc) {
+    const int j0 = g.goff[K], j1 = g.goff[K + 1];
+    const uint8_t* rec = g.rec + g.roff[K];
+    const int step = blockDim.x;
+    // two iterations of record and C loads in flight ahead of the arithmetic
+    using Raw = typename RecRaw<K>::type;
+    int j = j0 + threadIdx.x;
+    Raw r0{}, r1{};
+    TT c0 = TT(0), c1 = TT(0);
+    if (j < j1) { r0 = load_raw<K>(rec, j - j0); c0 = __ldcs(Cw + j); }
+    if (j + step < j1) { r1 = load_raw<K>(rec, j + step - j0); c1 = __ldcs(Cw + j + step); }
+    for (; j < j1; j += step) {
+        const Raw rc = r0;
+        const TT cu = c0;
+        r0 = r1;
+        c0 = c1;
+        const int jn = j + 2 * step;
+        if (jn < j1) { r1 = load_raw<K>(rec, jn - j0); c1 = __ldcs(Cw + jn); }
+        int h[K], p[K];
+        decode_rec<K>(rc, h, p);
+        TT d[NC];
+        bordered<K, NC, TT>(Ts, ld, xs, ys, ldy, s, h, p, d);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) acc.add(a, cu * d[a]);
+    }
+}
+
+struct RatioSmem {
+    size_t ts, ys, xd, xs, ph, red, total;
+};
+
+__host__ __device__ inline RatioSmem ratio_layout(int n, int m, int nch, int tt_bytes, int to_bytes) {
+    RatioSmem L;
+    auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
+    L.ts = 0;
+    L.ys = up(L.ts + (size_t)n * m * tt_bytes);
+    L.xd = up(L.ys + (size_t)nch * m * tt_bytes);
+    L.xs = up(L.xd + (size_t)n * 8);
+    L.ph = up(L.xs + (size_t)n * tt_bytes);
+    L.red = up(L.ph + (size_t)nch * n * to_bytes);
+    L.total = up(L.red + (size_t)32 * NCH * 8);
+    return L;
+}
+
+// FP32 variant: 3 resident blocks per SM (85 registers); only the rare k >= 5 paths spill.
+template <typename TO, typename TT, int NC>
+__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? 3 : 1) k_ratio(RatioArgs a, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n, m = a.m, N = a.N;
+    const RatioSmem L = ratio_layout(n, m, NC, sizeof(TT), sizeof(TO));
+    TT* Ts = reinterpret_cast<TT*>(smem + L.ts);
+    TT* ys = reinterpret_cast<TT*>(smem + L.ys);
+    double* xd = reinterpret_cast<double*>(smem + L.xd);
+    TT* xs = reinterpret_cast<TT*>(smem + L.xs);
+    TO* ph = reinterpret_cast<TO*>(smem + L.ph);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    __shared__ double s_s[NC];
+
+    const int w = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const TO* phw = static_cast<const TO*>(a.phi) + (long long)w * NC * N;
+    const double* Aw = a.Ainv + (long long)w * n * n;
+    for (int c = tid; c < n; c += bd) {
+        const double v = Aw[(long long)c * n + a.row];
+        xd[c] = v;
+        xs[c] = TT(v);
+    }
+    for (int idx = tid; idx < NC * n; idx += bd) {
+        const int al = idx / n, c = idx - al * n;
+        ph[idx] = phw[al * N + c];
+    }
+    copy_to_smem(Ts, static_cast<const TT*>(a.T) + (long long)w * n * m, (long long)n * m);
+    __syncthreads();
+    // A2: rho = phi_occ(r') . x and s^a = d^a phi_occ(r') . x (FP64)
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        if (warp < NC) {
+            double acc = 0.0;
+            for (int c = lane; c < n; c += 32) acc = fma(double(ph[warp * n + c]), xd[c], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) s_s[warp] = acc;
+        }
+    }
+    // A3: y^a = d^a phi_virt(r') - T^T d^a phi_occ(r')
+    for (int idx = tid; idx < NC * m; idx += bd) {
+        const int al = idx / m, av = idx - al * m;
+        TT acc = TT(phw[al * N + n + av]);
+        const TO* pa = ph + al * n;
+        for (int c = 0; c < n; ++c) acc = fma(-Ts[c * m + av], TT(pa[c]), acc);
+        ys[idx] = acc;
+        if (al == 0 && a.y0) static_cast<TT*>(a.y0)[(long long)w * m + av] = acc;
+    }
+    __syncthreads();
+    // A4 + A5: bordered determinants of every excitation, weighted by C
+    TT sT[NC];
+#pragma unroll
+    for (int al = 0; al < NC; ++al) sT[al] = TT(s_s[al]);
+    Accum<TT, NC> acc;
+    acc.zero();
+    const TT* Cw = static_cast<const TT*>(a.C) + (long long)w * a.g.n_exc;
+    for (int j = a.g.goff[0] + tid; j < a.g.goff[1]; j += bd) {
+        const TT cu = Cw[j];
+#pragma unroll
+        for (int al = 0; al < NC; ++al) acc.add(al, cu * sT[al]);
+    }
+    for (int k = 1; k <= a.g.kmax; ++k) {
+        switch (k) {
+            case 1: sweep_group<1, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 2: sweep_group<2, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 3: sweep_group<3, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 4: sweep_group<4, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 5: sweep_group<5, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 6: sweep_group<6, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 7: sweep_group<7, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+            case 8: sweep_group<8, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+        }
+    }
+    double v[NC];
+    acc.get(v);
+    block_sum<NC>(v, red);
+    if (tid == 0) {
+        const double num0 = v[0];
+        const double ratio = num0 / a.S[w];
+        a.ratio[(long long)w * a.rs] = ratio;
+        if constexpr (NC == 5) {
+            const double inv = 1.0 / num0;
+            for (int d = 0; d < 3; ++d) a.grad[(long long)w * a.gs + d] = v[1 + d] * inv;
+            a.lap[(long long)w * a.ls] = v[4] * inv;
+        }
+        if (a.rho) a.rho[w] = s_s[0];
+        if (a.num)
+            for (int al = 0; al < NCH; ++al) a.num[(long long)w * NCH + al] = al < NC ? v[al] : 0.0;
+        if (!isfinite(ratio)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// A6: accept -- Sherman-Morrison update of A_0^{-1} (FP64), rank-1 update of T (Section III)
+// ------------------------------------------------------------------------------------------
+// Ainv' = Ainv - x v^T / rho with v = phi_occ(r')^T Ainv - e_i^T, T' = T + x y^T / rho.
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict__ status) {
+    const int w = blockIdx.x;
+    if (!a.accept[w]) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n, m = a.m, tid = threadIdx.x, bd = blockDim.x;
+    double* xr = reinterpret_cast<double*>(smem);  // [n] x[c] / rho
+    double* pd = xr + n;                           // [n] phi_occ(r')
+    double* v = pd + n;                            // [n]
+    double* Aw = a.Ainv + (long long)w * n * n;
+    const TO* phw = static_cast<const TO*>(a.phi) + (long long)w * a.nch * a.N;
+    const double rho = a.rho[w];
+    const double irho = 1.0 / rho;
+    for (int c = tid; c < n; c += bd) {
+        xr[c] = Aw[(long long)c * n + a.row] * irho;
+        pd[c] = double(phw[c]);
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += bd) {
+        double acc = 0.0;
+        for (int c = 0; c < n; ++c) acc = fma(pd[c], Aw[(long long)c * n + r], acc);
+        v[r] = acc - (r == a.row ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (long long idx = tid; idx < (long long)n * n; idx += bd) {
+        const int c = int(idx / n), r = int(idx - (long long)c * n);
+        Aw[idx] = fma(-xr[c], v[r], Aw[idx]);
+    }
+    TT* Tw = static_cast<TT*>(a.T) + (long long)w * n * m;
+    const TT* yw = static_cast<const TT*>(a.y0) + (long long)w * m;
+    for (long long idx = tid; idx < (long long)n * m; idx += bd) {
+        const int c = int(idx / m), av = int(idx - (long long)c * m);
+        Tw[idx] = fma(TT(xr[c]), yw[av], Tw[idx]);
+    }
+    if (tid == 0) {
+        if (!(rho != 0.0) || !isfinite(rho)) atomicOr(status, ST_SINGULAR);
+        a.logdet[w] += log(fabs(rho));
+        if (rho < 0.0) a.sgn[w] = -a.sgn[w];
+        a.S[w] = a.num[(long long)w * NCH] * irho;
+        for (int d = 0; d < 3; ++d) a.R[((long long)w * a.n_tot + a.elec) * 3 + d] = a.rnew[w * 3 + d];
+    }
+}
+
+__global__ void k_propose(int W, int n_tot, int elec, const double* __restrict__ R, const double* __restrict__ eta,
+                          double tau, double* __restrict__ rnew) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * 3) return;
+    const int w = i / 3, d = i - w * 3;
+    rnew[i] = fma(tau, eta[i], R[((long long)w * n_tot + elec) * 3 + d]);
+}
+
+__global__ void k_metropolis(int W, const double* __restrict__ u, const double* __restrict__ ratio,
+                             uint8_t* __restrict__ accept) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const double r = ratio[w];
+    accept[w] = (u[w] < r * r) ? 1 : 0;
+}
+
+__global__ void k_state(int W, const double* __restrict__ ld0, const double* __restrict__ sg0,
+                        const double* __restrict__ ld1, const double* __restrict__ sg1, const double* __restrict__ S,
+                        double* __restrict__ logabs, double* __restrict__ sign) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const double s = S[w];
+    if (logabs) logabs[w] = ld0[w] + ld1[w] + log(fabs(s));
+    if (sign) sign[w] = sg0[w] * sg1[w] * (s < 0.0 ? -1.0 : (s > 0.0 ? 1.0 : 0.0));
+}
+
+template <typename Kern>
+void set_smem(Kern kern, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------------
+template <typename TO>
+static void orbitals_impl(const Launch& L, int nch, int P, int ppw, const double* pos, long long wstride, int p_off,
+                          const double4* bas, const int8_t* blm, int nb, const TO* B, int N, TO* out) {
+    if (P <= 0) return;
+    if (nch == 5) {
+        constexpr int PB = 8;
+        const size_t sm = (size_t)nb * PB * 5 * sizeof(TO);
+        set_smem(k_orbitals<TO, 5, PB>, sm);
+        L.count();
+        k_orbitals<TO, 5, PB><<<(P + PB - 1) / PB, 128, sm, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B,
+                                                                         N, out);
+    } else {
+        constexpr int PB = 16;
+        const size_t sm = (size_t)nb * PB * sizeof(TO);
+        set_smem(k_orbitals<TO, 1, PB>, sm);
+        L.count();
+        k_orbitals<TO, 1, PB><<<(P + PB - 1) / PB, 128, sm, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B,
+                                                                         N, out);
+    }
+}
+
+void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const double* pos, long long wstride,
+                     int p_off, const double4* bas, const int8_t* blm, int nb, const void* B, int N, void* out) {
+    if (mixed)
+        orbitals_impl<float>(L, nch, P, ppw, pos, wstride, p_off, bas, blm, nb, static_cast<const float*>(B), N,
+                             static_cast<float*>(out));
+    else
+        orbitals_impl<double>(L, nch, P, ppw, pos, wstride, p_off, bas, blm, nb, static_cast<const double*>(B), N,
+                              static_cast<double*>(out));
+}
+
+void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv, double* logdet,
+                    double* sgn) {
+    const size_t sm = (size_t)n * (n + 1) * 8 + (size_t)n * 8 + (size_t)n * 4 + 16;
+    if (mixed) {
+        set_smem(k_inverse<float>, sm);
+        L.count();
+        k_inverse<float><<<W, kBlock, sm, L.stream>>>(n, N, static_cast<const float*>(Phi), Ainv, logdet, sgn,
+                                                      L.status);
+    } else {
+        set_smem(k_inverse<double>, sm);
+        L.count();
+        k_inverse<double><<<W, kBlock, sm, L.stream>>>(n, N, static_cast<const double*>(Phi), Ainv, logdet, sgn,
+                                                       L.status);
+    }
+}
+
+void launch_table(const Launch& L, bool mixed, int W, int n, int N, const double* Ainv, const void* Phi, void* T) {
+    const int m = N - n;
+    if (m <= 0) return;
+    dim3 grid((m + 63) / 64, W);
+    if (mixed) {
+        const size_t sm = (((size_t)n * (n + 1) * 4 + 15) & ~size_t(15)) + (size_t)n * 64 * 4;
+        set_smem(k_table<float, float>, sm);
+        L.count();
+        k_table<float, float><<<grid, kBlock, sm, L.stream>>>(n, N, Ainv, static_cast<const float*>(Phi),
+                                                              static_cast<float*>(T));
+    } else {
+        const size_t sm = (((size_t)n * (n + 1) * 8 + 15) & ~size_t(15)) + (size_t)n * 64 * 8;
+        set_smem(k_table<double, double>, sm);
+        L.count();
+        k_table<double, double><<<grid, kBlock, sm, L.stream>>>(n, N, Ainv, static_cast<const double*>(Phi),
+                                                                static_cast<double*>(T));
+    }
+}
+
+void launch_exc_det(const Launch& L, bool mixed, int W, int n, int m, const ExcDev& g, const void* T, void* t) {
+    if (mixed) {
+        const size_t sm = (size_t)n * m * 4 + 16;
+        set_smem(k_exc_det<float>, sm);
+        L.count();
+        k_exc_det<float><<<W, kBlock, sm, L.stream>>>(n, m, g, static_cast<const float*>(T), static_cast<float*>(t));
+    } else {
+        const size_t sm = (size_t)n * m * 8 + 16;
+        set_smem(k_exc_det<double>, sm);
+        L.count();
+        k_exc_det<double><<<W, kBlock, sm, L.stream>>>(n, m, g, static_cast<const double*>(T),
+                                                       static_cast<double*>(t));
+    }
+}
+
+static constexpr int kHeavyLen = 128;
+
+void launch_ci_contract(const Launch& L, bool mixed, int W, int n_exc, int n_exc_other, const int* off,
+                        const int* other, const double* c, const void* t_other, void* C) {
+    dim3 grid((n_exc + kBlock - 1) / kBlock, W);
+    L.count();
+    if (mixed)
+        k_ci_contract_light<float><<<grid, kBlock, 0, L.stream>>>(n_exc, n_exc_other, off, other, c,
+                                                                  static_cast<const float*>(t_other),
+                                                                  static_cast<float*>(C), kHeavyLen);
+    else
+        k_ci_contract_light<double><<<grid, kBlock, 0, L.stream>>>(n_exc, n_exc_other, off, other, c,
+                                                                   static_cast<const double*>(t_other),
+                                                                   static_cast<double*>(C), kHeavyLen);
+}
+
+void launch_ci_contract_heavy(const Launch& L, bool mixed, int W, int n_exc, int n_exc_other, int n_heavy,
+                              const int* heavy, const int* off, const int* other, const double* c,
+                              const void* t_other, void* C) {
+    if (n_heavy <= 0) return;
+    dim3 grid(n_heavy, W);
+    L.count();
+    if (mixed)
+        k_ci_contract_heavy<float><<<grid, kBlock, 0, L.stream>>>(n_exc, n_exc_other, heavy, off, other, c,
+                                                                  static_cast<const float*>(t_other),
+                                                                  static_cast<float*>(C));
+    else
+        k_ci_contract_heavy<double><<<grid, kBlock, 0, L.stream>>>(n_exc, n_exc_other, heavy, off, other, c,
+                                                                   static_cast<const double*>(t_other),
+                                                                   static_cast<double*>(C));
+}
+
+int heavy_threshold() { return kHeavyLen; }
+
+void launch_ci_dot(const Launch& L, bool mixed, int W, int n_exc, const void* C, const void* t, double* S) {
+    L.count();
+    if (mixed)
+        k_ci_dot<float><<<W, kBlock, 0, L.stream>>>(n_exc, static_cast<const float*>(C), static_cast<const float*>(t),
+                                                    S);
+    else
+        k_ci_dot<double><<<W, kBlock, 0, L.stream>>>(n_exc, static_cast<const double*>(C),
+                                                     static_cast<const double*>(t), S);
+}
+
+size_t ratio_smem_bytes(bool mixed, int n, int m, int nch) {
+    return ratio_layout(n, m, nch, mixed ? 4 : 8, mixed ? 4 : 8).total;
+}
+
+template <typename TO, typename TT>
+static void ratio_impl(const Launch& L, const RatioArgs& a) {
+    const size_t sm = ratio_layout(a.n, a.m, a.nch, sizeof(TT), sizeof(TO)).total;
+    if (L.t0) cudaEventRecord(L.t0, L.stream);
+    if (a.nch == 5) {
+        set_smem(k_ratio<TO, TT, 5>, sm);
+        L.count();
+        k_ratio<TO, TT, 5><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
+    } else {
+        set_smem(k_ratio<TO, TT, 1>, sm);
+        L.count();
+        k_ratio<TO, TT, 1><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
+    }
+    if (L.t1) cudaEventRecord(L.t1, L.stream);
+}
+
+void launch_ratio(const Launch& L, bool mixed, const RatioArgs& a) {
+    if (mixed) ratio_impl<float, float>(L, a);
+    else ratio_impl<double, double>(L, a);
+}
+
+void launch_accept(const Launch& L, bool mixed, const AcceptArgs& a) {
+    const size_t sm = (size_t)a.n * 3 * 8;
+    L.count();
+    if (mixed) k_accept<float, float><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
+    else k_accept<double, double><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
+}
+
+void launch_propose(const Launch& L, int W, int n_tot, int elec, const double* R, const double* eta, double tau,
+                    double* rnew) {
+    L.count();
+    k_propose<<<(W * 3 + 255) / 256, 256, 0, L.stream>>>(W, n_tot, elec, R, eta, tau, rnew);
+}
+
+void launch_metropolis(const Launch& L, int W, const double* u, const double* ratio, uint8_t* accept) {
+    L.count();
+    k_metropolis<<<(W + 255) / 256, 256, 0, L.stream>>>(W, u, ratio, accept);
+}
+
+void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, const double* ld1, const double* sg1,
+                  const double* S, double* logabs, double* sign) {
+    L.count();
+    k_state<<<(W + 255) / 256, 256, 0, L.stream>>>(W, ld0, sg0, ld1, sg1, S, logabs, sign);
+}
+
+}  // namespace msd

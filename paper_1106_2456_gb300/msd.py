@@ -1,0 +1,296 @@
+"""Thin Python binding of libmsd (C ABI in ``include/msd.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libmsd.so``.  PyTorch provides device memory and the stream; tensors are passed to
+the library as raw device pointers.  Importing this module loads the library and
+raises if it has not been built; creating an :class:`MSD` raises without a GPU --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from .build import INCLUDE, library_path
+
+MSD_FP64, MSD_MIXED = 0, 1
+_STATUS = {0: "MSD_OK", 1: "MSD_ERR_ARG", 2: "MSD_ERR_CUDA", 3: "MSD_ERR_OOM", 4: "MSD_ERR_SINGULAR",
+           5: "MSD_ERR_TIMEOUT", 6: "MSD_ERR_STATE"}
+NCH = 5
+
+
+class MSDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("n_elec", ctypes.c_int32 * 2),
+        ("n_orb", ctypes.c_int32 * 2),
+        ("n_nuc", ctypes.c_int32),
+        ("nuc_xyz", ctypes.c_void_p),
+        ("n_basis", ctypes.c_int32),
+        ("bas_center", ctypes.c_void_p),
+        ("bas_lm", ctypes.c_void_p),
+        ("bas_alpha", ctypes.c_void_p),
+        ("B", ctypes.c_void_p * 2),
+        ("n_exc", ctypes.c_int32 * 2),
+        ("exc_off", ctypes.c_void_p * 2),
+        ("exc_holes", ctypes.c_void_p * 2),
+        ("exc_parts", ctypes.c_void_p * 2),
+        ("n_det", ctypes.c_int64),
+        ("det_up", ctypes.c_void_p),
+        ("det_dn", ctypes.c_void_p),
+        ("ci", ctypes.c_void_p),
+        ("n_walkers", ctypes.c_int32),
+        ("prec", ctypes.c_int32),
+        ("refresh_K", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+def header_functions():
+    """Names of the functions declared in include/msd.h."""
+    with open(os.path.join(INCLUDE, "msd.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(msd_[a-z_0-9]+)\s*\(", src)))
+
+
+_lib = None
+
+
+def load_library():
+    """Load libmsd.so (built by ``paper_1106_2456_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libmsd is not built ({path}); run paper_1106_2456_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "msd_init": ([vp, i32, vp], i32),
+        "msd_set_positions": ([vp, vp], i32),
+        "msd_ratio": ([vp, i32, vp, vp, vp, vp], i32),
+        "msd_accept": ([vp, i32, vp], i32),
+        "msd_grad_lap": ([vp, i32, vp, vp], i32),
+        "msd_eval_batch": ([vp, vp, vp, vp, vp, vp], i32),
+        "msd_get_state": ([vp, vp, vp, vp], i32),
+        "msd_propose": ([vp, i32, vp, d, vp], i32),
+        "msd_metropolis": ([vp, vp, vp, vp], i32),
+        "msd_ratio_host": ([vp, i32, vp, vp, vp, vp], i32),
+        "msd_accept_host": ([vp, i32, vp], i32),
+        "msd_set_stream": ([vp, vp], i32),
+        "msd_sync": ([vp], i32),
+        "msd_last_error": ([vp], ctypes.c_char_p),
+        "msd_exc_histogram": ([vp, i32, vp], i32),
+        "msd_copy_state": ([vp, i32, i32, vp, vp], i32),
+        "msd_timing_start": ([vp], i32),
+        "msd_timing_stop": ([vp, vp, vp, vp], i32),
+        "msd_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, shape=None, name: str = "") -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+class MSD:
+    """One libmsd context: a multi-determinant wavefunction and W walkers on the current GPU."""
+
+    def __init__(self, problem, n_walkers: int, precision: str = "fp64", refresh_K: int = 1 << 30,
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise MSDError(2, "a CUDA GPU is required (libmsd has no CPU path)")
+        self.lib = load_library()
+        self.p = problem
+        self.W = int(n_walkers)
+        self.n_tot = problem.n_tot
+        self.mixed = precision == "mixed"
+        if precision not in ("fp64", "mixed"):
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            if a.size == 0:
+                a = np.zeros(1, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        s = _Problem()
+        s.n_elec[0], s.n_elec[1] = problem.n_elec
+        s.n_orb[0], s.n_orb[1] = problem.n_orb
+        s.n_nuc = problem.nuc_xyz.shape[0]
+        s.nuc_xyz = arr(problem.nuc_xyz, np.float64)
+        s.n_basis = problem.n_basis
+        s.bas_center = arr(problem.bas_center, np.int32)
+        s.bas_lm = arr(problem.bas_lm, np.int8)
+        s.bas_alpha = arr(problem.bas_alpha, np.float64)
+        for k in range(2):
+            s.B[k] = arr(problem.B[k], np.float64)
+            s.n_exc[k] = problem.n_exc(k)
+            s.exc_off[k] = arr(problem.exc_off[k], np.int32)
+            s.exc_holes[k] = arr(problem.exc_holes[k], np.uint8)
+            s.exc_parts[k] = arr(problem.exc_parts[k], np.uint8)
+        s.n_det = problem.n_det
+        s.det_up = arr(problem.det_up, np.int32)
+        s.det_dn = arr(problem.det_dn, np.int32)
+        s.ci = arr(problem.ci, np.float64)
+        s.n_walkers = self.W
+        s.prec = MSD_MIXED if self.mixed else MSD_FP64
+        s.refresh_K = int(min(refresh_K, 2 ** 31 - 1))
+        s.cuda_stream = self.stream.cuda_stream
+        ctx = ctypes.c_void_p()
+        rc = self.lib.msd_init(ctypes.byref(s), 1, ctypes.byref(ctx))
+        if rc != 0:
+            raise MSDError(rc, self.lib.msd_last_error(None).decode())
+        self.ctx = ctx
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    # -- helpers -----------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise MSDError(rc, self.lib.msd_last_error(self.ctx).decode())
+
+    def _empty(self, *shape, dtype=torch.float64):
+        return torch.empty(shape, dtype=dtype, device=self.dev)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.msd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points --------------------------------------------------------------------
+    def set_positions(self, R: torch.Tensor):
+        self._check(self.lib.msd_set_positions(self.ctx, _dptr(R, torch.float64, (self.W, self.n_tot, 3), "R")))
+
+    def ratio_into(self, elec: int, rnew: torch.Tensor, ratio: torch.Tensor, grad: Optional[torch.Tensor] = None,
+                   lap: Optional[torch.Tensor] = None):
+        W = self.W
+        self._check(self.lib.msd_ratio(self.ctx, int(elec), _dptr(rnew, torch.float64, (W, 3), "rnew"),
+                                       _dptr(ratio, torch.float64, (W,), "ratio"),
+                                       _dptr(grad, torch.float64, (W, 3), "grad"),
+                                       _dptr(lap, torch.float64, (W,), "lap")))
+
+    def ratio(self, elec: int, rnew: torch.Tensor, with_grad: bool = True):
+        r = self._empty(self.W)
+        g = self._empty(self.W, 3) if with_grad else None
+        l = self._empty(self.W) if with_grad else None
+        self.ratio_into(elec, rnew, r, g, l)
+        return r, g, l
+
+    def accept(self, elec: int, accept: torch.Tensor):
+        self._check(self.lib.msd_accept(self.ctx, int(elec), _dptr(accept, torch.uint8, (self.W,), "accept")))
+
+    def grad_lap(self, elec: int = -1):
+        if elec >= 0:
+            g, l = self._empty(self.W, 3), self._empty(self.W)
+        else:
+            g, l = self._empty(self.W, self.n_tot, 3), self._empty(self.W, self.n_tot)
+        self._check(self.lib.msd_grad_lap(self.ctx, int(elec), g.data_ptr(), l.data_ptr()))
+        return g, l
+
+    def eval_batch(self, R: torch.Tensor, with_grad: bool = False):
+        la, sg = self._empty(self.W), self._empty(self.W)
+        g = self._empty(self.W, self.n_tot, 3) if with_grad else None
+        l = self._empty(self.W, self.n_tot) if with_grad else None
+        self._check(self.lib.msd_eval_batch(self.ctx, _dptr(R, torch.float64, (self.W, self.n_tot, 3), "R"),
+                                            la.data_ptr(), sg.data_ptr(),
+                                            g.data_ptr() if g is not None else None,
+                                            l.data_ptr() if l is not None else None))
+        return la, sg, g, l
+
+    def get_state(self):
+        R = self._empty(self.W, self.n_tot, 3)
+        la, sg = self._empty(self.W), self._empty(self.W)
+        self._check(self.lib.msd_get_state(self.ctx, R.data_ptr(), la.data_ptr(), sg.data_ptr()))
+        return R, la, sg
+
+    def propose(self, elec: int, eta: torch.Tensor, tau: float, out: torch.Tensor):
+        self._check(self.lib.msd_propose(self.ctx, int(elec), _dptr(eta, torch.float64, (self.W, 3), "eta"),
+                                         float(tau), _dptr(out, torch.float64, (self.W, 3), "out")))
+
+    def metropolis(self, u: torch.Tensor, ratio: torch.Tensor, out: torch.Tensor):
+        self._check(self.lib.msd_metropolis(self.ctx, _dptr(u, torch.float64, (self.W,), "u"),
+                                            _dptr(ratio, torch.float64, (self.W,), "ratio"),
+                                            _dptr(out, torch.uint8, (self.W,), "out")))
+
+    def ratio_host(self, elec: int, rnew: np.ndarray, ratio: np.ndarray, grad: Optional[np.ndarray] = None,
+                   lap: Optional[np.ndarray] = None):
+        """Host-buffer walker-move step (numpy arrays, ideally in pinned memory)."""
+        self._check(self.lib.msd_ratio_host(self.ctx, int(elec), rnew.ctypes.data, ratio.ctypes.data,
+                                            grad.ctypes.data if grad is not None else None,
+                                            lap.ctypes.data if lap is not None else None))
+
+    def accept_host(self, elec: int, accept: np.ndarray):
+        self._check(self.lib.msd_accept_host(self.ctx, int(elec), accept.ctypes.data))
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self.lib.msd_set_stream(self.ctx, stream.cuda_stream))
+
+    def sync(self):
+        self._check(self.lib.msd_sync(self.ctx))
+
+    _ITEMS = {"R": 0, "Ainv": 1, "T": 2, "logdet": 3, "sign": 4, "S": 5, "C": 6, "t": 7, "rho": 8, "num": 9,
+              "y0": 10, "phi": 11}
+
+    def copy_state(self, item: str, spin: int = 0) -> torch.Tensor:
+        """A copy of one piece of the walker state (see msd_copy_state in include/msd.h)."""
+        code = self._ITEMS[item]
+        nbytes = ctypes.c_int64()
+        self._check(self.lib.msd_copy_state(self.ctx, code, int(spin), None, ctypes.byref(nbytes)))
+        small = self.mixed and item in ("T", "C", "t", "y0", "phi")
+        dt = torch.float32 if small else torch.float64
+        out = torch.empty(nbytes.value // (4 if small else 8), dtype=dt, device=self.dev)
+        self._check(self.lib.msd_copy_state(self.ctx, code, int(spin), out.data_ptr(), None))
+        return out.view(self.W, -1)
+
+    def timing_start(self):
+        self._check(self.lib.msd_timing_start(self.ctx))
+
+    def timing_stop(self):
+        """(summed excitation-sweep kernel time in ms, its launches, all kernel launches)."""
+        ms = ctypes.c_double()
+        n1 = ctypes.c_int64()
+        n2 = ctypes.c_int64()
+        self._check(self.lib.msd_timing_stop(self.ctx, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
+        return ms.value, n1.value, n2.value
+
+    def exc_histogram(self, spin: int) -> np.ndarray:
+        out = np.zeros(1 + 9, dtype=np.int64)
+        self._check(self.lib.msd_exc_histogram(self.ctx, int(spin), out.ctypes.data))
+        return out

@@ -1,0 +1,222 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on replayed Metropolis trajectories.
+
+Every ratio, gradient component and laplacian X is compared as
+|X_gpu - X_oracle| <= tol(kappa) * max(|X_oracle|, cancellation scale of X), with kappa the
+largest condition number of the reference Slater matrices involved in the move:
+FP64: tol = 1e-10 for kappa <= 3e3, growing as 3.3e-14 kappa beyond (the table method
+forms every quantity through A_0^{-1}; Section V names this instability);
+mixed: tol = 1e3 * 2^-24 * max(kappa, 10).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1106_2456_gb300 import msd, workloads as wl
+from _parity import rel_err, replay
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _assert(out, tol, what):
+    for key in ("ratio", "grad", "lap"):
+        worst = max(out[key + "_n"])
+        i = int(np.argmax(out[key + "_n"]))
+        assert worst <= 1.0, (f"{what}: {key} error {out[key][i]:.3e} at step {i} exceeds the bar "
+                              f"(kappa {out['kappa'][i]:.2e}) by {worst:.2f}x")
+    # log|Psi| errors in units of the bar (the final value accumulates one log|rho| per
+    # accepted move between refreshes, hence 100 bars)
+    assert out["logabs0"] <= 1.0, f"{what}: initial log|Psi| off by {out['logabs0']:.2f} bars"
+    assert out["sign0_ok"] and out["sign_final_ok"]
+    assert out["R_final_err"] == 0.0
+    assert out["logabs_final"] <= 1.0, f"{what}: final log|Psi| off by {out['logabs_final']:.2f} x 100 bars"
+
+
+def test_water_fp64_every_move():
+    """Water-like system: every move of 50 sweeps of 64 walkers (refresh every 5 steps)."""
+    w = wl.make_workload("water")
+    out = replay(w, "fp64", n_steps=50 * w.problem.n_tot)
+    _assert(out, FP64_TOL, "water fp64")
+    assert 0.2 < np.mean(out["accept"]) < 0.95
+
+
+def test_water_fp64_no_refresh():
+    """Sherman-Morrison updates only (refresh period longer than the run)."""
+    w = wl.make_workload("water")
+    out = replay(w, "fp64", n_steps=10 * w.problem.n_tot, refresh_K=10 ** 9)
+    _assert(out, FP64_TOL, "water fp64 without refresh")
+
+
+def test_water_mixed_every_move():
+    w = wl.make_workload("water")
+    out = replay(w, "mixed", n_steps=10 * w.problem.n_tot)
+    _assert(out, MIXED_TOL, "water mixed")
+
+
+def test_medium_fp64_sampled():
+    """32 + 32 electrons, 1e4 determinants, 1024 walkers; 6 walkers checked over 72 moves
+    (crossing the spin boundary and one refresh of each spin)."""
+    w = wl.make_workload("medium")
+    out = replay(w, "fp64", n_steps=72, check=[0, 1, 333, 640, 1000, 1023])
+    _assert(out, FP64_TOL, "medium fp64")
+
+
+def test_medium_mixed_sampled():
+    w = wl.make_workload("medium")
+    out = replay(w, "mixed", n_steps=40, check=[5, 517, 1023])
+    _assert(out, MIXED_TOL, "medium mixed")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_large_sampled(prec, tol):
+    """Headline size (64 + 64 electrons, 256 orbitals, 1e5 determinants, 4096 walkers, the
+    launch configuration the benchmark times): 2 walkers checked over moves of electrons
+    0, 1, 63 (spin up) and 64, 65 (spin down)."""
+    w = wl.make_workload("large")
+    out = replay(w, prec, n_steps=5, check=[0, 4095], elec_order=[0, 1, 63, 64, 65])
+    _assert(out, tol, f"large {prec}")
+
+
+@pytest.mark.parametrize("orders", [wl.uniform_orders(1, 8), wl.geometric_orders(1, 8)])
+def test_all_orders_ragged(orders):
+    """Every excitation order 1..8, odd sizes (n = 11/9, m = 14/17, 37 walkers), all moves."""
+    w = wl.custom_workload((11, 9), (25, 26), 700, orders, W=37, n_nuc=4, seed=11, K=7)
+    out = replay(w, "fp64", n_steps=2 * w.problem.n_tot)
+    _assert(out, FP64_TOL, "orders 1..8 fp64")
+    out = replay(w, "mixed", n_steps=w.problem.n_tot)
+    _assert(out, MIXED_TOL, "orders 1..8 mixed")
+
+
+def test_single_determinant_and_no_virtuals():
+    """n_det = 1 (canonical Slater): ratio = Sherman-Morrison denominator; also N = n."""
+    base = wl.make_workload("water", n_walkers=9)
+    p = base.problem
+    single = wl.explicit_problem(p.nuc_xyz, p.bas_center, p.bas_lm, p.bas_alpha, p.B, p.n_elec,
+                                 [((), ())], [((), ())], [0], [0], [1.0])
+    w = wl.dataclasses.replace(base, problem=single)
+    out = replay(w, "fp64", n_steps=20)
+    _assert(out, FP64_TOL, "single determinant")
+    B0 = (np.ascontiguousarray(p.B[0][:, :5]), np.ascontiguousarray(p.B[1][:, :5]))
+    novirt = wl.explicit_problem(p.nuc_xyz, p.bas_center, p.bas_lm, p.bas_alpha, B0, p.n_elec,
+                                 [((), ())], [((), ())], [0], [0], [2.5])
+    w = wl.dataclasses.replace(base, problem=novirt)
+    out = replay(w, "fp64", n_steps=20)
+    _assert(out, FP64_TOL, "no virtual orbitals")
+
+
+def test_one_walker_one_electron_per_spin():
+    w = wl.custom_workload((1, 1), (6, 4), 9, wl.uniform_orders(1, 2), W=1, n_nuc=2, seed=3, K=3)
+    out = replay(w, "fp64", n_steps=12)
+    _assert(out, FP64_TOL, "1+1 electrons")
+
+
+def test_grad_lap_and_eval_batch_at_current_positions():
+    w = wl.make_workload("water", n_walkers=24)
+    p = w.problem
+    ctx = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    R = torch.tensor(w.R0, device="cuda")
+    ctx.set_positions(R)
+    orc = oracle.Oracle(p)
+    g_all, l_all = ctx.grad_lap(-1)
+    g_all, l_all = g_all.cpu().numpy(), l_all.cpu().numpy()
+    for e in range(p.n_tot):
+        ref = orc.eval(w.R0, e)
+        assert rel_err(g_all[:, e], ref["grad"], ref["absum"][:, 1:4]).max() <= FP64_TOL
+        assert rel_err(l_all[:, e], ref["lap"], ref["absum"][:, 4]).max() <= FP64_TOL
+        g1, l1 = ctx.grad_lap(e)
+        assert np.array_equal(g1.cpu().numpy(), g_all[:, e]) and np.array_equal(l1.cpu().numpy(), l_all[:, e])
+    # from-scratch evaluation at other positions leaves the walker state alone
+    R2 = R + 0.05
+    la, sg, g, l = ctx.eval_batch(R2, with_grad=True)
+    ref = orc.eval(R2.cpu().numpy())
+    assert np.max(np.abs(la.cpu().numpy() - ref["logabs"])) < 1e-10
+    assert np.array_equal(sg.cpu().numpy(), ref["sign"])
+    e = 6
+    ref_e = orc.eval(R2.cpu().numpy(), e)
+    assert rel_err(g.cpu().numpy()[:, e], ref_e["grad"], ref_e["absum"][:, 1:4]).max() <= FP64_TOL
+    Rg, la0, _ = ctx.get_state()
+    assert torch.equal(Rg, R)
+    ref0 = orc.eval(w.R0)
+    assert np.max(np.abs(la0.cpu().numpy() - ref0["logabs"])) < 1e-10
+    ctx.close()
+
+
+def test_host_twins_match_device_calls():
+    w = wl.make_workload("water", n_walkers=16)
+    p = w.problem
+    a = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    b = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    R = torch.tensor(w.R0, device="cuda")
+    a.set_positions(R)
+    b.set_positions(R)
+    eta, u = w.proposals(8)
+    Rh = w.R0.copy()
+    for t in range(8):
+        e = t % p.n_tot
+        rnew = np.ascontiguousarray(Rh[:, e] + w.tau * eta[t])
+        r1, g1, l1 = a.ratio(e, torch.tensor(rnew, device="cuda"))
+        r2, g2, l2 = np.zeros(w.n_walkers), np.zeros((w.n_walkers, 3)), np.zeros(w.n_walkers)
+        b.ratio_host(e, rnew, r2, g2, l2)
+        assert np.array_equal(r1.cpu().numpy(), r2)
+        assert np.array_equal(g1.cpu().numpy(), g2) and np.array_equal(l1.cpu().numpy(), l2)
+        acc = (u[t] < r2 * r2).astype(np.uint8)
+        a.accept(e, torch.tensor(acc, device="cuda"))
+        b.accept_host(e, acc)
+        Rh[acc.astype(bool), e] = rnew[acc.astype(bool)]
+    a.close()
+    b.close()
+
+
+def test_propose_and_metropolis_helpers():
+    w = wl.make_workload("water", n_walkers=32)
+    ctx = msd.MSD(w.problem, w.n_walkers, "fp64")
+    R = torch.tensor(w.R0, device="cuda")
+    ctx.set_positions(R)
+    eta = torch.randn(w.n_walkers, 3, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(eta)
+    ctx.propose(4, eta, 0.3, out)
+    assert torch.allclose(out, R[:, 4] + 0.3 * eta, rtol=0, atol=1e-15)
+    ratio = torch.linspace(-2, 2, w.n_walkers, dtype=torch.float64, device="cuda")
+    u = torch.rand(w.n_walkers, dtype=torch.float64, device="cuda")
+    acc = torch.empty(w.n_walkers, dtype=torch.uint8, device="cuda")
+    ctx.metropolis(u, ratio, acc)
+    assert torch.equal(acc.bool(), u < ratio * ratio)
+    ctx.close()
+
+
+def test_error_paths_without_faults():
+    w = wl.make_workload("water", n_walkers=8)
+    p = w.problem
+    ctx = msd.MSD(p, w.n_walkers, "fp64")
+    R = torch.tensor(w.R0, device="cuda")
+    rnew = torch.zeros(w.n_walkers, 3, dtype=torch.float64, device="cuda")
+    ratio = torch.empty(w.n_walkers, dtype=torch.float64, device="cuda")
+    with pytest.raises(msd.MSDError, match="MSD_ERR_STATE"):
+        ctx.ratio_into(0, rnew, ratio)  # before set_positions
+    ctx.set_positions(R)
+    with pytest.raises(msd.MSDError, match="MSD_ERR_STATE"):
+        ctx.accept(0, torch.ones(w.n_walkers, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(msd.MSDError, match="MSD_ERR_ARG"):
+        ctx.ratio_into(p.n_tot, rnew, ratio)
+    ctx.ratio_into(1, R[:, 1].contiguous(), ratio)
+    with pytest.raises(msd.MSDError, match="MSD_ERR_STATE"):
+        ctx.accept(2, torch.ones(w.n_walkers, dtype=torch.uint8, device="cuda"))
+    ctx.sync()
+    # two spin-up electrons at one point: A_0 is singular, reported on msd_sync
+    R2 = R.clone()
+    R2[:, 1] = R2[:, 0]
+    ctx.set_positions(R2)
+    with pytest.raises(msd.MSDError, match="MSD_ERR_SINGULAR"):
+        ctx.sync()
+    ctx.sync()  # status cleared
+    ctx.close()

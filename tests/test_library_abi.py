@@ -1,0 +1,143 @@
+"""The C ABI library without a GPU: it loads, exports every declared symbol, and rejects bad
+problems on the host before any CUDA call (argument validation needs no device)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_1106_2456_gb300 import build as libbuild
+from paper_1106_2456_gb300 import msd, workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return msd.load_library()
+
+
+def test_exports_every_declared_function(lib):
+    names = msd.header_functions()
+    assert "msd_init" in names and "msd_ratio" in names and "msd_accept" in names
+    assert "msd_grad_lap" in names and "msd_eval_batch" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def _struct(problem, W=4, prec=0, K=5):
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dtype=dt)
+        if a.size == 0:
+            a = np.zeros(1, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    s = msd._Problem()
+    s.n_elec[0], s.n_elec[1] = problem.n_elec
+    s.n_orb[0], s.n_orb[1] = problem.n_orb
+    s.n_nuc = problem.nuc_xyz.shape[0]
+    s.nuc_xyz = arr(problem.nuc_xyz, np.float64)
+    s.n_basis = problem.n_basis
+    s.bas_center = arr(problem.bas_center, np.int32)
+    s.bas_lm = arr(problem.bas_lm, np.int8)
+    s.bas_alpha = arr(problem.bas_alpha, np.float64)
+    for k in range(2):
+        s.B[k] = arr(problem.B[k], np.float64)
+        s.n_exc[k] = problem.n_exc(k)
+        s.exc_off[k] = arr(problem.exc_off[k], np.int32)
+        s.exc_holes[k] = arr(problem.exc_holes[k], np.uint8)
+        s.exc_parts[k] = arr(problem.exc_parts[k], np.uint8)
+    s.n_det = problem.n_det
+    s.det_up = arr(problem.det_up, np.int32)
+    s.det_dn = arr(problem.det_dn, np.int32)
+    s.ci = arr(problem.ci, np.float64)
+    s.n_walkers = W
+    s.prec = prec
+    s.refresh_K = K
+    s.cuda_stream = None
+    return s, keep
+
+
+def _init_status(lib, s, n_systems=1):
+    ctx = ctypes.c_void_p()
+    rc = lib.msd_init(ctypes.byref(s), n_systems, ctypes.byref(ctx))
+    return rc, lib.msd_last_error(None).decode()
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (lambda s, k: setattr(s, "n_walkers", 0), "n_walkers"),
+    (lambda s, k: setattr(s, "refresh_K", 0), "refresh_K"),
+    (lambda s, k: setattr(s, "prec", 7), "precision"),
+    (lambda s, k: s.n_elec.__setitem__(0, 0), "n_elec"),
+    (lambda s, k: s.n_orb.__setitem__(1, 3), "n_orb"),
+    (lambda s, k: setattr(s, "n_det", 0), "term"),
+])
+def test_init_rejects_bad_arguments(lib, mutate, needle):
+    w = wl.make_workload("water", n_walkers=4)
+    s, keep = _struct(w.problem)
+    mutate(s, keep)
+    rc, msg = _init_status(lib, s)
+    assert rc == 1 and needle in msg
+
+
+def test_init_rejects_bad_strings(lib):
+    w = wl.make_workload("water", n_walkers=4)
+    p = w.problem
+    # particle index beyond the virtuals
+    bad = wl.dataclasses.replace(p, exc_parts=(p.exc_parts[0].copy(), p.exc_parts[1].copy()))
+    bad.exc_parts[0][0] = 200
+    s, keep = _struct(bad)
+    rc, msg = _init_status(lib, s)
+    assert rc == 1 and "out of range" in msg
+    # holes not ascending
+    off = p.exc_off[0]
+    u = int(np.nonzero(np.diff(off) >= 2)[0][0])
+    holes = p.exc_holes[0].copy()
+    holes[off[u]], holes[off[u] + 1] = holes[off[u] + 1], holes[off[u]]
+    bad = wl.dataclasses.replace(p, exc_holes=(holes, p.exc_holes[1]))
+    s, keep = _struct(bad)
+    rc, msg = _init_status(lib, s)
+    assert rc == 1 and "ascending" in msg
+    # a term pointing past the strings
+    du = p.det_up.copy()
+    du[3] = p.n_exc(0)
+    s, keep = _struct(wl.dataclasses.replace(p, det_up=du))
+    rc, msg = _init_status(lib, s)
+    assert rc == 1 and "missing string" in msg
+    # the reference must come first
+    off2 = p.exc_off[1].copy()
+    s, keep = _struct(p)
+    fake = np.concatenate([[0], off2[1:] + 1]).astype(np.int32)
+    keep.append(fake)
+    s.exc_off[1] = fake.ctypes.data
+    rc, msg = _init_status(lib, s)
+    assert rc == 1
+
+
+def test_init_rejects_batched_systems(lib):
+    w = wl.make_workload("water", n_walkers=4)
+    s, keep = _struct(w.problem)
+    rc, msg = _init_status(lib, s, n_systems=3)
+    assert rc == 1 and "n_systems" in msg
+
+
+def test_init_rejects_table_larger_than_shared_memory(lib):
+    w = wl.make_workload("water", n_walkers=4)
+    s, keep = _struct(w.problem)
+    s.n_elec[0] = 200
+    s.n_orb[0] = 400
+    rc, msg = _init_status(lib, s)
+    assert rc == 1
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.msd_init(None, 1, None) == 1
+    assert lib.msd_sync(None) == 1
+    assert lib.msd_ratio(None, 0, None, None, None, None) == 1
+    lib.msd_destroy(None)  # no-op
+
+
+def test_graft_build_entry():
+    __graft_entry__.build()
