@@ -102,6 +102,13 @@ typedef struct msd_ctx msd_ctx;
  * device, and allocates all per-walker state.  *out is NULL on failure. */
 msd_status msd_init(const msd_problem* prob, int32_t n_systems, msd_ctx** out);
 
+/* Validate a problem and report, without any CUDA call, the device layout msd_init would
+ * build: for spin s, out[16 s + 0] = internal string count (singles may form a dense n x m
+ * block), [1] = 1 if they do, [2] = largest order, [3] = strings whose CI weight sums more
+ * than a threshold number of terms, [4] = bytes of excitation records, [5 .. 14] = first
+ * internal index of each order 0..8 and the end, [15] = terms referenced.  out has 32 entries. */
+msd_status msd_describe(const msd_problem* prob, int64_t* out);
+
 /* Set the walker positions R_dev [W][n_tot][3] and build the state from scratch:
  * orbitals, LU of A_0 (A_0^{-1}, log|det A_0|, sign), T = A_0^{-1} Phi_virt and the CI
  * sums (Section III: initial inverse and determinants computed from scratch). */

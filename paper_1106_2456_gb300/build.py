@@ -20,6 +20,9 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 BUILDDIR = os.path.join(PKG, "_build")
 SOURCES = ["msd_kernels.cu", "msd_api.cu"]
+# host-only translation units keep libstdc++ bounds assertions on (an out-of-range index
+# aborts with a message instead of corrupting the heap)
+HOST_CHECKED = {"msd_api.cu": ["-Xcompiler", "-D_GLIBCXX_ASSERTIONS"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -68,7 +71,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: Optional[List
 
     def one(src: str) -> str:
         obj = os.path.join(BUILDDIR, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        extra = HOST_CHECKED.get(src, [])
+        cmd = [cc, *flags, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

@@ -33,6 +33,10 @@ struct SpinConst {
     double* t_c = nullptr;        // [n_det]
     int* heavy = nullptr;         // strings with many terms
     int n_heavy = 0;
+    // host-side plan, uploaded by upload_spin
+    std::vector<uint8_t> h_rec;
+    std::vector<int> h_toff, h_tother, h_heavy;
+    std::vector<double> h_tc;
 };
 
 struct State {
@@ -215,16 +219,24 @@ msd_status validate(const msd_problem* p) {
     return MSD_OK;
 }
 
-// Build device strings of spin s, grouped by order and sorted within each order.
-msd_status build_strings(msd_ctx* c, const msd_problem* p, int s) {
-    SpinConst& S = c->sp[s];
+// Build device strings of spin s, grouped by order and sorted within each order.  Singles
+// become a dense n x m block of internal indices when at least a quarter of them are present.
+msd_status plan_strings(SpinConst& S, const msd_problem* p, int s) {
     const int ne = p->n_exc[s];
     const int32_t* off = p->exc_off[s];
+    auto order_of = [&](int u) { return off[u + 1] - off[u]; };
+    S.hist.assign(MAXK + 1, 0);
+    S.g.kmax = 0;
+    for (int u = 0; u < ne; ++u) {
+        S.hist[order_of(u)]++;
+        S.g.kmax = std::max(S.g.kmax, order_of(u));
+    }
+    const bool dense1 = S.hist[1] > 0 && 4 * S.hist[1] >= (long long)S.n * S.m;
+    S.g.dense1 = dense1 ? 1 : 0;
     std::vector<int> order(ne);
     std::iota(order.begin(), order.end(), 0);
     auto key_less = [&](int a, int b) {
-        const int ka = off[a + 1] - off[a], kb = off[b + 1] - off[b];
-        if (a == 0 || b == 0) return a == 0 && b != 0;  // the reference stays first
+        const int ka = order_of(a), kb = order_of(b);
         if (ka != kb) return ka < kb;
         for (int q = 0; q < ka; ++q) {
             const int ha = p->exc_holes[s][off[a] + q], hb = p->exc_holes[s][off[b] + q];
@@ -236,37 +248,37 @@ msd_status build_strings(msd_ctx* c, const msd_problem* p, int s) {
         }
         return a < b;
     };
-    std::stable_sort(order.begin(), order.end(), key_less);
-    S.user_of = order;
-    S.internal_of.assign(ne, 0);
-    for (int i = 0; i < ne; ++i) S.internal_of[order[i]] = i;
-    S.hist.assign(MAXK + 1, 0);
-    S.g.n_exc = ne;
-    S.g.kmax = 0;
-    for (int k = 0; k <= MAXK + 1; ++k) S.g.goff[k] = 0;
-    std::vector<int> kof(ne);
-    for (int i = 0; i < ne; ++i) {
-        const int u = order[i];
-        kof[i] = off[u + 1] - off[u];
-        S.hist[kof[i]]++;
-        S.g.kmax = std::max(S.g.kmax, kof[i]);
-    }
-    // group boundaries: goff[k] = first internal index of order >= k
-    int acc = 0;
+    std::stable_sort(order.begin(), order.end(), key_less);  // the reference (k = 0, index 0) stays first
+    S.internal_of.assign(ne, -1);
+    int idx = 0, pos = 0;
     for (int k = 0; k <= MAXK; ++k) {
-        S.g.goff[k] = acc;
-        acc += (int)S.hist[k];
+        S.g.goff[k] = idx;
+        if (k == 1 && dense1) {
+            for (; pos < ne && order_of(order[pos]) == 1; ++pos) {
+                const int u = order[pos];
+                S.internal_of[u] = idx + p->exc_holes[s][off[u]] * S.m + p->exc_parts[s][off[u]];
+            }
+            idx += S.n * S.m;
+            continue;
+        }
+        for (; pos < ne && order_of(order[pos]) == k; ++pos) S.internal_of[order[pos]] = idx++;
     }
-    S.g.goff[MAXK + 1] = acc;
-    // records
+    S.g.goff[MAXK + 1] = idx;
+    S.g.n_exc = idx;
+    S.user_of.assign(idx, -1);
+    for (int u = 0; u < ne; ++u) S.user_of[S.internal_of[u]] = u;
+    // records of the groups processed one excitation per thread
     std::vector<uint8_t> rec;
     for (int k = 0; k <= MAXK + 1; ++k) S.g.roff[k] = 0;
+    pos = 0;
     for (int k = 1; k <= MAXK; ++k) {
         while (rec.size() % 16) rec.push_back(0);
         S.g.roff[k] = (long long)rec.size();
+        if (k == 1 && dense1) continue;
         const int rb = rec_bytes(k);
-        for (int i = S.g.goff[k]; i < S.g.goff[k + 1]; ++i) {
+        for (int i = 0; i < ne; ++i) {
             const int u = order[i];
+            if (order_of(u) != k) continue;
             const size_t base = rec.size();
             rec.resize(base + rb, 0);
             for (int q = 0; q < k; ++q) {
@@ -276,17 +288,14 @@ msd_status build_strings(msd_ctx* c, const msd_problem* p, int s) {
         }
     }
     while (rec.size() % 16) rec.push_back(0);
-    uint8_t* d_rec = nullptr;
-    TRY(upload(c, &d_rec, rec.data(), rec.size()));
-    S.g.rec = d_rec;
+    S.h_rec.swap(rec);
+    S.g.rec = nullptr;
     return MSD_OK;
 }
 
 // Terms grouped by the internal string of spin s (the moving spin), for C_s.
-msd_status build_terms(msd_ctx* c, const msd_problem* p, int s) {
-    SpinConst& S = c->sp[s];
-    const SpinConst& O = c->sp[1 - s];
-    const int ne = p->n_exc[s];
+msd_status plan_terms(SpinConst& S, const SpinConst& O, const msd_problem* p, int s) {
+    const int ne = S.g.n_exc;  // internal strings (a dense singles block counts n m)
     const int64_t nd = p->n_det;
     const int32_t* mine = s == 0 ? p->det_up : p->det_dn;
     const int32_t* oth = s == 0 ? p->det_dn : p->det_up;
@@ -305,11 +314,40 @@ msd_status build_terms(msd_ctx* c, const msd_problem* p, int s) {
     std::vector<int> heavy;
     for (int u = 0; u < ne; ++u)
         if (off[u + 1] - off[u] > heavy_threshold()) heavy.push_back(u);
-    TRY(upload(c, &S.t_off, off.data(), off.size()));
-    TRY(upload(c, &S.t_other, other.data(), other.size()));
-    TRY(upload(c, &S.t_c, cc.data(), cc.size()));
-    S.n_heavy = (int)heavy.size();
-    TRY(upload(c, &S.heavy, heavy.data(), heavy.size()));
+    S.h_toff.swap(off);
+    S.h_tother.swap(other);
+    S.h_tc.swap(cc);
+    S.h_heavy.swap(heavy);
+    S.n_heavy = (int)S.h_heavy.size();
+    return MSD_OK;
+}
+
+// Host plan of both spins: validation already done; no CUDA call.
+msd_status plan_problem(SpinConst (&sp)[2], const msd_problem* p) {
+    for (int s = 0; s < 2; ++s) {
+        sp[s].n = p->n_elec[s];
+        sp[s].N = p->n_orb[s];
+        sp[s].m = p->n_orb[s] - p->n_elec[s];
+        sp[s].off = s ? p->n_elec[0] : 0;
+        TRY(plan_strings(sp[s], p, s));
+    }
+    for (int s = 0; s < 2; ++s) TRY(plan_terms(sp[s], sp[1 - s], p, s));
+    return MSD_OK;
+}
+
+msd_status upload_spin(msd_ctx* c, SpinConst& S) {
+    uint8_t* d_rec = nullptr;
+    TRY(upload(c, &d_rec, S.h_rec.data(), S.h_rec.size()));
+    S.g.rec = d_rec;
+    TRY(upload(c, &S.t_off, S.h_toff.data(), S.h_toff.size()));
+    TRY(upload(c, &S.t_other, S.h_tother.data(), S.h_tother.size()));
+    TRY(upload(c, &S.t_c, S.h_tc.data(), S.h_tc.size()));
+    TRY(upload(c, &S.heavy, S.h_heavy.data(), S.h_heavy.size()));
+    std::vector<uint8_t>().swap(S.h_rec);
+    std::vector<int>().swap(S.h_toff);
+    std::vector<int>().swap(S.h_tother);
+    std::vector<double>().swap(S.h_tc);
+    std::vector<int>().swap(S.h_heavy);
     return MSD_OK;
 }
 
@@ -419,13 +457,11 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
         msd_destroy(c);
         return s;
     };
-    for (int s = 0; s < 2; ++s) {
-        c->sp[s].n = p->n_elec[s];
-        c->sp[s].N = p->n_orb[s];
-        c->sp[s].m = p->n_orb[s] - p->n_elec[s];
-        c->sp[s].off = s ? p->n_elec[0] : 0;
-    }
     msd_status st;
+    if ((st = plan_problem(c->sp, p)) != MSD_OK) {
+        c->err = g_init_error;
+        return bail(st);
+    }
     // basis
     std::vector<double4> bas(c->nb);
     for (int mu = 0; mu < c->nb; ++mu) {
@@ -447,10 +483,8 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
             if ((st = upload(c, &d, p->B[s], cnt)) != MSD_OK) return bail(st);
             S.B = d;
         }
-        if ((st = build_strings(c, p, s)) != MSD_OK) return bail(st);
+        if ((st = upload_spin(c, S)) != MSD_OK) return bail(st);
     }
-    for (int s = 0; s < 2; ++s)
-        if ((st = build_terms(c, p, s)) != MSD_OK) return bail(st);
     const int nmax = std::max(c->sp[0].n, c->sp[1].n);
     const int Nmax = std::max(c->sp[0].N, c->sp[1].N);
     const int mmax = std::max(std::max(c->sp[0].m, c->sp[1].m), 1);
@@ -469,6 +503,25 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(c, MSD_ERR_CUDA, "memset"));
     if ((st = alloc_state(c, c->st)) != MSD_OK) return bail(st);
     *out = c;
+    return MSD_OK;
+}
+
+msd_status msd_describe(const msd_problem* p, int64_t* out) {
+    g_init_error.clear();
+    if (!out) return fail(nullptr, MSD_ERR_ARG, "out is NULL");
+    TRY(validate(p));
+    SpinConst sp[2];
+    TRY(plan_problem(sp, p));
+    for (int s = 0; s < 2; ++s) {
+        int64_t* o = out + 16 * s;
+        o[0] = sp[s].g.n_exc;
+        o[1] = sp[s].g.dense1;
+        o[2] = sp[s].g.kmax;
+        o[3] = sp[s].n_heavy;
+        o[4] = (int64_t)sp[s].h_rec.size();
+        for (int k = 0; k <= MAXK + 1; ++k) o[5 + k] = sp[s].g.goff[k];
+        o[15] = (int64_t)sp[s].h_toff.back();
+    }
     return MSD_OK;
 }
 

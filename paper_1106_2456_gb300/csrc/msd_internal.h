@@ -25,10 +25,13 @@ __host__ __device__ constexpr int rec_bytes(int k) {
 // Excitation strings of one spin on the device, grouped by order.  Internal index i of
 // order k lies in [goff[k], goff[k+1]); group 0 holds the reference.  Group k's records
 // start at byte roff[k] of rec.  Within a group strings are sorted lexicographically by
-// (holes, particles) so consecutive threads share table rows.
+// (holes, particles) so consecutive threads share table rows.  With dense1 set the singles
+// occupy a dense n x m block (index goff[1] + h m + p; absent singles carry C = 0) and have
+// no records.
 struct ExcDev {
     int n_exc = 0;
     int kmax = 0;
+    int dense1 = 0;
     int goff[MAXK + 2] = {0};
     long long roff[MAXK + 2] = {0};
     const uint8_t* rec = nullptr;

@@ -403,7 +403,11 @@ __global__ void __launch_bounds__(kBlock) k_exc_det(int n, int m, ExcDev g, cons
     __syncthreads();
     TT* tw = t + (long long)w * g.n_exc;
     for (int j = g.goff[0] + threadIdx.x; j < g.goff[1]; j += blockDim.x) tw[j] = TT(1);
-    for (int k = 1; k <= g.kmax; ++k) {
+    if (g.dense1) {
+        // singles laid out densely: internal index goff[1] + h m + p holds T[h][p]
+        for (int q = threadIdx.x; q < n * m; q += blockDim.x) tw[g.goff[1] + q] = Ts[q];
+    }
+    for (int k = g.dense1 ? 2 : 1; k <= g.kmax; ++k) {
         switch (k) {
             case 1: det_group<1, TT>(g, Ts, m, tw); break;
             case 2: det_group<2, TT>(g, Ts, m, tw); break;
@@ -468,18 +472,31 @@ __global__ void __launch_bounds__(kBlock) k_ci_dot(int n_exc, const TT* __restri
 }
 
 // ------------------------------------------------------------------------------------------
-// A2-A5: reference ratio, virtual-row contraction, excitation sweep and CI reduction
+// A2-A5: reference ratio, excitation sweep, virtual-row contraction and CI reduction
 // ------------------------------------------------------------------------------------------
-template <int K, int NC, typename TT>
-__device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int ld, const TT* xs, const TT* ys,
-                                            int ldy, const TT (&s)[NC], const TT* __restrict__ Cw,
-                                            Accum<TT, NC>& acc) {
+// Every channel a shares T_u and x_u, so with d^a_u = det(T_u) s^a + y^a_u . z_u,
+// z_u = adj(T_u) x_u:
+//   sum_u C_u d^a_u = s^a S_T + sum_p y^a[p] G[p],
+//   S_T = sum_u C_u det T_u,   G[p] = sum over (u, slot l with p_l = p) of C_u z_u[l].
+// The sweep therefore builds one m-vector G and one scalar S_T per walker; the five channels
+// are five length-m dot products afterwards.  Singles are a dense n x m block when most are
+// present: G1[p] = sum_h C1[h][p] x[h], S_T += sum_{h,p} C1[h][p] T[h][p].
+constexpr int kWarps = kBlock / 32;
+
+template <int K, typename TT, int NGW>
+__device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int ld, const TT* xs,
+                                            const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int base) {
     const int j0 = g.goff[K], j1 = g.goff[K + 1];
     const uint8_t* rec = g.rec + g.roff[K];
     const int step = blockDim.x;
+    TT* Gmine = Gw + ((threadIdx.x >> 5) % NGW) * ld;
+    // Threads stride over the concatenation of all groups from `base` on, so the remainder of
+    // each group lands on different threads and the per-thread work stays balanced.
+    const int rot = (j0 - base) % step;
+    const int first = (int(threadIdx.x) - rot + step) % step;
     // two iterations of record and C loads in flight ahead of the arithmetic
     using Raw = typename RecRaw<K>::type;
-    int j = j0 + threadIdx.x;
+    int j = j0 + first;
     Raw r0{}, r1{};
     TT c0 = TT(0), c1 = TT(0);
     if (j < j1) { r0 = load_raw<K>(rec, j - j0); c0 = __ldcs(Cw + j); }
@@ -493,41 +510,56 @@ __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int l
         if (jn < j1) { r1 = load_raw<K>(rec, jn - j0); c1 = __ldcs(Cw + jn); }
         int h[K], p[K];
         decode_rec<K>(rc, h, p);
-        TT d[NC];
-        bordered<K, NC, TT>(Ts, ld, xs, ys, ldy, s, h, p, d);
+        TT det, z[K];
+        adj_solve<K, TT>(Ts, ld, xs, h, p, det, z);
+        sacc.add(0, cu * det);
 #pragma unroll
-        for (int a = 0; a < NC; ++a) acc.add(a, cu * d[a]);
+        for (int l = 0; l < K; ++l) atomicAdd(Gmine + p[l], cu * z[l]);
     }
 }
 
 struct RatioSmem {
-    size_t ts, ys, xd, xs, ph, red, total;
+    size_t ts, xd, xs, ph, g1, gw, red, total;
 };
 
-__host__ __device__ inline RatioSmem ratio_layout(int n, int m, int nch, int tt_bytes, int to_bytes) {
+__host__ __device__ inline RatioSmem ratio_layout(int n, int m, int nch, int tt_bytes, int to_bytes, int ngw) {
     RatioSmem L;
     auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t mm = (size_t)(m > 0 ? m : 1);
     L.ts = 0;
-    L.ys = up(L.ts + (size_t)n * m * tt_bytes);
-    L.xd = up(L.ys + (size_t)nch * m * tt_bytes);
+    L.xd = up(L.ts + (size_t)n * m * tt_bytes);
     L.xs = up(L.xd + (size_t)n * 8);
     L.ph = up(L.xs + (size_t)n * tt_bytes);
-    L.red = up(L.ph + (size_t)nch * n * to_bytes);
-    L.total = up(L.red + (size_t)32 * NCH * 8);
+    L.g1 = up(L.ph + (size_t)nch * n * to_bytes);
+    L.gw = up(L.g1 + mm * tt_bytes);
+    L.red = up(L.gw + (size_t)ngw * mm * tt_bytes);
+    L.total = up(L.red + (size_t)32 * (NCH + 1) * 8);
     return L;
 }
 
-// FP32 variant: 3 resident blocks per SM (85 registers); only the rare k >= 5 paths spill.
+// Copies of G per block: one per warp in FP32 (deterministic), one per warp pair in FP64 so two
+// blocks of 256 threads fit an SM.
+template <typename TT>
+__host__ __device__ constexpr int ratio_ngw() {
+    return sizeof(TT) == 4 ? kWarps : kWarps / 2;
+}
+
+#ifndef MSD_RATIO_F32_BLOCKS
+#define MSD_RATIO_F32_BLOCKS 3
+#endif
 template <typename TO, typename TT, int NC>
-__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? 3 : 1) k_ratio(RatioArgs a, int* __restrict__ status) {
+__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
+    k_ratio(RatioArgs a, int* __restrict__ status) {
+    constexpr int NGW = ratio_ngw<TT>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, m = a.m, N = a.N;
-    const RatioSmem L = ratio_layout(n, m, NC, sizeof(TT), sizeof(TO));
+    const RatioSmem L = ratio_layout(n, m, NC, sizeof(TT), sizeof(TO), NGW);
     TT* Ts = reinterpret_cast<TT*>(smem + L.ts);
-    TT* ys = reinterpret_cast<TT*>(smem + L.ys);
     double* xd = reinterpret_cast<double*>(smem + L.xd);
     TT* xs = reinterpret_cast<TT*>(smem + L.xs);
     TO* ph = reinterpret_cast<TO*>(smem + L.ph);
+    TT* G1 = reinterpret_cast<TT*>(smem + L.g1);
+    TT* Gw = reinterpret_cast<TT*>(smem + L.gw);
     double* red = reinterpret_cast<double*>(smem + L.red);
     __shared__ double s_s[NC];
 
@@ -543,6 +575,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? 3 : 1) k_ratio(Ratio
         const int al = idx / n, c = idx - al * n;
         ph[idx] = phw[al * N + c];
     }
+    for (int q = tid; q < (m > 0 ? m : 1); q += bd) G1[q] = TT(0);
+    for (int q = tid; q < NGW * (m > 0 ? m : 1); q += bd) Gw[q] = TT(0);
     copy_to_smem(Ts, static_cast<const TT*>(a.T) + (long long)w * n * m, (long long)n * m);
     __syncthreads();
     // A2: rho = phi_occ(r') . x and s^a = d^a phi_occ(r') . x (FP64)
@@ -555,55 +589,85 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? 3 : 1) k_ratio(Ratio
             if (lane == 0) s_s[warp] = acc;
         }
     }
-    // A3: y^a = d^a phi_virt(r') - T^T d^a phi_occ(r')
-    for (int idx = tid; idx < NC * m; idx += bd) {
-        const int al = idx / m, av = idx - al * m;
-        TT acc = TT(phw[al * N + n + av]);
-        const TO* pa = ph + al * n;
-        for (int c = 0; c < n; ++c) acc = fma(-Ts[c * m + av], TT(pa[c]), acc);
-        ys[idx] = acc;
-        if (al == 0 && a.y0) static_cast<TT*>(a.y0)[(long long)w * m + av] = acc;
-    }
-    __syncthreads();
-    // A4 + A5: bordered determinants of every excitation, weighted by C
-    TT sT[NC];
-#pragma unroll
-    for (int al = 0; al < NC; ++al) sT[al] = TT(s_s[al]);
-    Accum<TT, NC> acc;
-    acc.zero();
+    // A4: S_T and G over every excitation
+    Accum<TT, 1> sacc;
+    sacc.zero();
     const TT* Cw = static_cast<const TT*>(a.C) + (long long)w * a.g.n_exc;
-    for (int j = a.g.goff[0] + tid; j < a.g.goff[1]; j += bd) {
-        const TT cu = Cw[j];
+    for (int j = a.g.goff[0] + tid; j < a.g.goff[1]; j += bd) sacc.add(0, Cw[j]);
+    if (a.g.dense1) {
+        // column p of the dense singles block: G1[p] = sum_h C1[h][p] x[h], S_T += C1[h][p] T[h][p];
+        // eight rows per round so eight loads of the C stream are in flight per thread
+        const TT* C1 = Cw + a.g.goff[1];
+        for (int pv = tid; pv < m; pv += bd) {
+            TT g = TT(0), st = TT(0);
+            int h = 0;
+            for (; h + 8 <= n; h += 8) {
+                TT c[8];
 #pragma unroll
-        for (int al = 0; al < NC; ++al) acc.add(al, cu * sT[al]);
-    }
-    for (int k = 1; k <= a.g.kmax; ++k) {
-        switch (k) {
-            case 1: sweep_group<1, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 2: sweep_group<2, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 3: sweep_group<3, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 4: sweep_group<4, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 5: sweep_group<5, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 6: sweep_group<6, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 7: sweep_group<7, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
-            case 8: sweep_group<8, NC, TT>(a.g, Ts, m, xs, ys, m, sT, Cw, acc); break;
+                for (int q = 0; q < 8; ++q) c[q] = __ldcs(C1 + (h + q) * m + pv);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    g = fma(c[q], xs[h + q], g);
+                    st = fma(c[q], Ts[(h + q) * m + pv], st);
+                }
+            }
+            for (; h < n; ++h) {
+                const TT c = __ldcs(C1 + h * m + pv);
+                g = fma(c, xs[h], g);
+                st = fma(c, Ts[h * m + pv], st);
+            }
+            G1[pv] = g;
+            sacc.add(0, st);
         }
     }
-    double v[NC];
-    acc.get(v);
-    block_sum<NC>(v, red);
+    const int base = a.g.goff[a.g.dense1 ? 2 : 1];
+    for (int k = a.g.dense1 ? 2 : 1; k <= a.g.kmax; ++k) {
+        switch (k) {
+            case 1: sweep_group<1, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 2: sweep_group<2, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 3: sweep_group<3, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 4: sweep_group<4, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 5: sweep_group<5, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 6: sweep_group<6, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 7: sweep_group<7, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 8: sweep_group<8, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+        }
+    }
+    __syncthreads();
+    // A3 + A5: y^a[p] = d^a phi_virt(r')[p] - sum_c T[c][p] d^a phi_occ(r')[c], contracted with G
+    double v[NC + 1];
+#pragma unroll
+    for (int al = 0; al < NC; ++al) v[al] = 0.0;
+    v[NC] = sacc.get(0);
+    for (int pv = tid; pv < m; pv += bd) {
+        TT gp = G1[pv];
+#pragma unroll
+        for (int q = 0; q < NGW; ++q) gp += Gw[q * m + pv];
+#pragma unroll
+        for (int al = 0; al < NC; ++al) {
+            TT y = TT(phw[al * N + n + pv]);
+            const TO* pa = ph + al * n;
+            for (int c = 0; c < n; ++c) y = fma(-Ts[c * m + pv], TT(pa[c]), y);
+            if (al == 0 && a.y0) static_cast<TT*>(a.y0)[(long long)w * m + pv] = y;
+            v[al] = fma(double(y), double(gp), v[al]);
+        }
+    }
+    block_sum<NC + 1>(v, red);
     if (tid == 0) {
-        const double num0 = v[0];
-        const double ratio = num0 / a.S[w];
+        const double ST = v[NC];
+        double num[NC];
+#pragma unroll
+        for (int al = 0; al < NC; ++al) num[al] = fma(s_s[al], ST, v[al]);
+        const double ratio = num[0] / a.S[w];
         a.ratio[(long long)w * a.rs] = ratio;
         if constexpr (NC == 5) {
-            const double inv = 1.0 / num0;
-            for (int d = 0; d < 3; ++d) a.grad[(long long)w * a.gs + d] = v[1 + d] * inv;
-            a.lap[(long long)w * a.ls] = v[4] * inv;
+            const double inv = 1.0 / num[0];
+            for (int d = 0; d < 3; ++d) a.grad[(long long)w * a.gs + d] = num[1 + d] * inv;
+            a.lap[(long long)w * a.ls] = num[4] * inv;
         }
         if (a.rho) a.rho[w] = s_s[0];
         if (a.num)
-            for (int al = 0; al < NCH; ++al) a.num[(long long)w * NCH + al] = al < NC ? v[al] : 0.0;
+            for (int al = 0; al < NCH; ++al) a.num[(long long)w * NCH + al] = al < NC ? num[al] : 0.0;
         if (!isfinite(ratio)) atomicOr(status, ST_NONFINITE);
     }
 }
@@ -817,12 +881,13 @@ void launch_ci_dot(const Launch& L, bool mixed, int W, int n_exc, const void* C,
 }
 
 size_t ratio_smem_bytes(bool mixed, int n, int m, int nch) {
-    return ratio_layout(n, m, nch, mixed ? 4 : 8, mixed ? 4 : 8).total;
+    return mixed ? ratio_layout(n, m, nch, 4, 4, ratio_ngw<float>()).total
+                 : ratio_layout(n, m, nch, 8, 8, ratio_ngw<double>()).total;
 }
 
 template <typename TO, typename TT>
 static void ratio_impl(const Launch& L, const RatioArgs& a) {
-    const size_t sm = ratio_layout(a.n, a.m, a.nch, sizeof(TT), sizeof(TO)).total;
+    const size_t sm = ratio_layout(a.n, a.m, a.nch, sizeof(TT), sizeof(TO), ratio_ngw<TT>()).total;
     if (L.t0) cudaEventRecord(L.t0, L.stream);
     if (a.nch == 5) {
         set_smem(k_ratio<TO, TT, 5>, sm);

@@ -1,6 +1,15 @@
-// msd_smalldet.cuh -- small determinants of excitation-table entries (Section III) and the
-// bordered determinants of a single-electron move (Section IV-A/IV-C), as __host__ __device__
-// code so the same arithmetic can be unit-tested on the host.
+// msd_smalldet.cuh -- small determinants of excitation-table entries (Section III), as
+// __host__ __device__ code so the arithmetic the excitation sweep runs can be unit-tested on
+// the host.
+//
+// For an excitation u of order k with holes h_q and particles p_l, T_u[q][l] = T[h_q][p_l].
+//   small_det : det T_u                               (= det A_u / det A_0, Section III)
+//   adj_solve : det T_u and z = adj(T_u) x_u          (the two ingredients of every bordered
+//               determinant det [[T_u, x_u], [-y^T, s]] = det(T_u) s + y . z, Section IV-A/C)
+// Both use an LU with partial pivoting held in registers.  Closed-form cofactor expansions
+// are not used for k >= 2: when A_0 is nearly singular, T = A_0^{-1} Phi_virt carries a large
+// rank-1 component and products of its entries cancel catastrophically, while the pivoted
+// elimination removes that component in its first step.
 #pragma once
 
 #include <cmath>
@@ -26,96 +35,122 @@ MSD_HD T tabs(T x) {
     return x < T(0) ? -x : x;
 }
 
-// det T_u by LU with partial pivoting held in registers (k >= 2).  Closed-form cofactor
-// expansions are not used: when A_0 is nearly singular, T = A_0^{-1} Phi_virt carries a large
-// rank-1 component and products of its entries cancel catastrophically, while the pivoted
-// elimination removes that component in its first step.
+// 1 / x: correctly rounded reciprocal (FP32 on the device avoids the IEEE division sequence).
+MSD_HD double recip(double x) { return 1.0 / x; }
+MSD_HD float recip(float x) {
+#if defined(__CUDA_ARCH__)
+    return __frcp_rn(x);
+#else
+    return 1.0f / x;
+#endif
+}
+
+// In-register LU with partial pivoting of the K x K block M; the right-hand side b is
+// permuted and eliminated alongside.  On return M holds U above the diagonal and 1/u_kk on it;
+// the return value is det M; `singular` is set if a pivot is exactly zero.
+template <int K, typename TT>
+MSD_HD TT lu_inplace(TT (&M)[K][K], TT (&b)[K], bool& singular) {
+    TT det = TT(1);
+    singular = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int piv = k;
+        TT best = tabs(M[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < K; ++r) {
+            const TT v = tabs(M[r][k]);
+            if (v > best) {
+                best = v;
+                piv = r;
+            }
+        }
+#pragma unroll
+        for (int r = k + 1; r < K; ++r) {
+            const bool sw = (piv == r);
+#pragma unroll
+            for (int j = k; j < K; ++j) {
+                const TT x = M[k][j], y = M[r][j];
+                M[k][j] = sw ? y : x;
+                M[r][j] = sw ? x : y;
+            }
+            const TT x = b[k], y = b[r];
+            b[k] = sw ? y : x;
+            b[r] = sw ? x : y;
+        }
+        const TT pv = M[k][k];
+        det = (piv != k) ? -det * pv : det * pv;
+        singular |= (pv == TT(0));
+        const TT ip = recip(pv);
+#pragma unroll
+        for (int r = k + 1; r < K; ++r) {
+            const TT fct = M[r][k] * ip;
+#pragma unroll
+            for (int j = k + 1; j < K; ++j) M[r][j] = fma(-fct, M[k][j], M[r][j]);
+            b[r] = fma(-fct, b[k], b[r]);
+        }
+        M[k][k] = ip;
+    }
+    return det;
+}
+
+// det T_u.
 template <int K, typename TT>
 MSD_HD TT small_det(const TT* Ts, int ld, const int (&h)[K], const int (&p)[K]) {
     if constexpr (K == 1) {
         return Ts[h[0] * ld + p[0]];
     } else {
-        TT M[K][K];
+        TT M[K][K], b[K];
 #pragma unroll
-        for (int q = 0; q < K; ++q)
+        for (int q = 0; q < K; ++q) {
+            b[q] = TT(0);
 #pragma unroll
             for (int l = 0; l < K; ++l) M[q][l] = Ts[h[q] * ld + p[l]];
-        TT det = TT(1);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            int piv = k;
-            TT best = tabs(M[k][k]);
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const TT v = tabs(M[r][k]);
-                if (v > best) { best = v; piv = r; }
-            }
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const bool sw = (piv == r);
-#pragma unroll
-                for (int j = k; j < K; ++j) {
-                    const TT x = M[k][j], y = M[r][j];
-                    M[k][j] = sw ? y : x;
-                    M[r][j] = sw ? x : y;
-                }
-            }
-            const TT pv = M[k][k];
-            det = (piv != k) ? -det * pv : det * pv;
-            if (pv == TT(0)) return TT(0);
-            const TT ip = TT(1) / pv;
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const TT fct = M[r][k] * ip;
-#pragma unroll
-                for (int j = k + 1; j < K; ++j) M[r][j] = fma(-fct, M[k][j], M[r][j]);
-            }
         }
-        return det;
+        bool singular;
+        const TT det = lu_inplace<K, TT>(M, b, singular);
+        return singular ? TT(0) : det;
     }
 }
 
-// Slow path for an exactly singular T_u (k >= 4): the (k+1) x (k+1) bordered determinant of
-// each channel by its own LU.  Never taken for generic inputs.
+// Exactly singular T_u: z_l = det(T_u with column l replaced by x_u) (Cramer's rule for the
+// adjugate), each by its own pivoted LU.  Never taken for generic inputs.
 template <typename TT>
-MSD_HD_NOINLINE TT bordered_direct(int K, const TT* Ts, int ld, const TT* xs, const TT* ysa, const int* h,
-                                           const int* p, TT s) {
-    TT M[MSD_MAX_ORDER + 1][MSD_MAX_ORDER + 1];
-    const int n1 = K + 1;
-    for (int q = 0; q < K; ++q) {
-        for (int l = 0; l < K; ++l) M[q][l] = Ts[h[q] * ld + p[l]];
-        M[q][K] = xs[h[q]];
-    }
-    for (int l = 0; l < K; ++l) M[K][l] = -ysa[p[l]];
-    M[K][K] = s;
-    TT det = TT(1);
-    for (int k = 0; k < n1; ++k) {
-        int piv = k;
-        TT best = tabs(M[k][k]);
-        for (int r = k + 1; r < n1; ++r)
-            if (tabs(M[r][k]) > best) { best = tabs(M[r][k]); piv = r; }
-        if (best == TT(0)) return TT(0);
-        if (piv != k) {
-            for (int j = 0; j < n1; ++j) { TT t = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = t; }
-            det = -det;
+MSD_HD_NOINLINE void adj_cramer(int K, const TT* Ts, int ld, const TT* xs, const int* h, const int* p, TT* z) {
+    TT M[MSD_MAX_ORDER][MSD_MAX_ORDER];
+    for (int l = 0; l < K; ++l) {
+        for (int q = 0; q < K; ++q)
+            for (int j = 0; j < K; ++j) M[q][j] = (j == l) ? xs[h[q]] : Ts[h[q] * ld + p[j]];
+        TT det = TT(1);
+        for (int k = 0; k < K && det != TT(0); ++k) {
+            int piv = k;
+            for (int r = k + 1; r < K; ++r)
+                if (tabs(M[r][k]) > tabs(M[piv][k])) piv = r;
+            if (M[piv][k] == TT(0)) {
+                det = TT(0);
+                break;
+            }
+            if (piv != k) {
+                for (int j = 0; j < K; ++j) {
+                    const TT t = M[k][j];
+                    M[k][j] = M[piv][j];
+                    M[piv][j] = t;
+                }
+                det = -det;
+            }
+            det *= M[k][k];
+            for (int r = k + 1; r < K; ++r) {
+                const TT fct = M[r][k] / M[k][k];
+                for (int j = k + 1; j < K; ++j) M[r][j] -= fct * M[k][j];
+            }
         }
-        det *= M[k][k];
-        for (int r = k + 1; r < n1; ++r) {
-            const TT fct = M[r][k] / M[k][k];
-            for (int j = k + 1; j < n1; ++j) M[r][j] -= fct * M[k][j];
-        }
+        z[l] = det;
     }
-    return det;
 }
 
-// Bordered determinants d^a = det [[T_u, x_u], [-y^a_u^T, s^a]] = det(T_u) s^a + y^a_u . adj(T_u) x_u
-// for NC channels sharing one factorisation of T_u (adj(T_u) x_u = det(T_u) T_u^{-1} x_u from
-// the pivoted LU).  ys is [NC][ldy].
-template <int K, int NC, typename TT>
-MSD_HD void bordered(const TT* Ts, int ld, const TT* xs, const TT* ys, int ldy,
-                                         const TT (&s)[NC], const int (&h)[K], const int (&p)[K], TT (&d)[NC]) {
-    TT z[K];  // adj(T_u) x_u, indexed by particle slot
-    TT det;
+// det T_u and z = adj(T_u) x_u = det(T_u) T_u^{-1} x_u, z indexed by particle slot l.
+template <int K, typename TT>
+MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], const int (&p)[K], TT& det,
+                      TT (&z)[K]) {
     if constexpr (K == 1) {
         det = Ts[h[0] * ld + p[0]];
         z[0] = xs[h[0]];
@@ -127,54 +162,23 @@ MSD_HD void bordered(const TT* Ts, int ld, const TT* xs, const TT* ys, int ldy,
             for (int l = 0; l < K; ++l) M[q][l] = Ts[h[q] * ld + p[l]];
             b[q] = xs[h[q]];
         }
-        det = TT(1);
-        bool singular = false;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            int piv = k;
-            TT best = tabs(M[k][k]);
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const TT v = tabs(M[r][k]);
-                if (v > best) { best = v; piv = r; }
-            }
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const bool sw = (piv == r);
-#pragma unroll
-                for (int j = k; j < K; ++j) {
-                    const TT x = M[k][j], y = M[r][j];
-                    M[k][j] = sw ? y : x;
-                    M[r][j] = sw ? x : y;
-                }
-                const TT x = b[k], y = b[r];
-                b[k] = sw ? y : x;
-                b[r] = sw ? x : y;
-            }
-            const TT pv = M[k][k];
-            det = (piv != k) ? -det * pv : det * pv;
-            singular |= (pv == TT(0));
-            const TT ip = TT(1) / pv;
-#pragma unroll
-            for (int r = k + 1; r < K; ++r) {
-                const TT fct = M[r][k] * ip;
-#pragma unroll
-                for (int j = k + 1; j < K; ++j) M[r][j] = fma(-fct, M[k][j], M[r][j]);
-                b[r] = fma(-fct, b[k], b[r]);
-            }
-            M[k][k] = ip;
-        }
+        bool singular;
+        det = lu_inplace<K, TT>(M, b, singular);
         if (singular) {
             int hh[MSD_MAX_ORDER], pp[MSD_MAX_ORDER];
+            TT zz[MSD_MAX_ORDER];
 #pragma unroll
             for (int q = 0; q < K; ++q) {
                 hh[q] = h[q];
                 pp[q] = p[q];
             }
-            for (int a = 0; a < NC; ++a) d[a] = bordered_direct<TT>(K, Ts, ld, xs, ys + a * ldy, hh, pp, s[a]);
+            adj_cramer<TT>(K, Ts, ld, xs, hh, pp, zz);
+            det = TT(0);
+#pragma unroll
+            for (int q = 0; q < K; ++q) z[q] = zz[q];
             return;
         }
-        // back substitution U z' = b, then z = det * z'
+        // back substitution U z' = b', then z = det z'
 #pragma unroll
         for (int q = K - 1; q >= 0; --q) {
             TT acc = b[q];
@@ -185,37 +189,25 @@ MSD_HD void bordered(const TT* Ts, int ld, const TT* xs, const TT* ys, int ldy,
 #pragma unroll
         for (int q = 0; q < K; ++q) z[q] *= det;
     }
-#pragma unroll
-    for (int a = 0; a < NC; ++a) {
-        TT acc = det * s[a];
-#pragma unroll
-        for (int l = 0; l < K; ++l) acc = fma(ys[a * ldy + p[l]], z[l], acc);
-        d[a] = acc;
-    }
 }
 
-// Per-thread accumulators of the CI sums: plain FP64, or FP32 with Kahan compensation.
-template <typename TT, int NC>
+// Per-thread accumulators of CI sums: plain FP64, or FP32 with Kahan compensation.
+template <typename TT, int NV>
 struct Accum;
-template <int NC>
-struct Accum<double, NC> {
-    double s[NC];
+template <int NV>
+struct Accum<double, NV> {
+    double s[NV];
     MSD_HD void zero() {
-#pragma unroll
-        for (int a = 0; a < NC; ++a) s[a] = 0.0;
+        for (int a = 0; a < NV; ++a) s[a] = 0.0;
     }
     MSD_HD void add(int a, double x) { s[a] += x; }
-    MSD_HD void get(double (&v)[NC]) const {
-#pragma unroll
-        for (int a = 0; a < NC; ++a) v[a] = s[a];
-    }
+    MSD_HD double get(int a) const { return s[a]; }
 };
-template <int NC>
-struct Accum<float, NC> {
-    float s[NC], c[NC];
+template <int NV>
+struct Accum<float, NV> {
+    float s[NV], c[NV];
     MSD_HD void zero() {
-#pragma unroll
-        for (int a = 0; a < NC; ++a) s[a] = c[a] = 0.0f;
+        for (int a = 0; a < NV; ++a) s[a] = c[a] = 0.0f;
     }
     MSD_HD void add(int a, float x) {
         const float y = x - c[a];
@@ -223,10 +215,7 @@ struct Accum<float, NC> {
         c[a] = (t - s[a]) - y;
         s[a] = t;
     }
-    MSD_HD void get(double (&v)[NC]) const {
-#pragma unroll
-        for (int a = 0; a < NC; ++a) v[a] = double(s[a]) - double(c[a]);
-    }
+    MSD_HD double get(int a) const { return double(s[a]) - double(c[a]); }
 };
 
 }  // namespace msd

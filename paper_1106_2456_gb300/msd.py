@@ -79,6 +79,7 @@ def load_library():
     vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     sig = {
         "msd_init": ([vp, i32, vp], i32),
+        "msd_describe": ([vp, vp], i32),
         "msd_set_positions": ([vp, vp], i32),
         "msd_ratio": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_accept": ([vp, i32, vp], i32),

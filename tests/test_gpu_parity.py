@@ -167,8 +167,11 @@ def test_host_twins_match_device_calls():
         r1, g1, l1 = a.ratio(e, torch.tensor(rnew, device="cuda"))
         r2, g2, l2 = np.zeros(w.n_walkers), np.zeros((w.n_walkers, 3)), np.zeros(w.n_walkers)
         b.ratio_host(e, rnew, r2, g2, l2)
-        assert np.array_equal(r1.cpu().numpy(), r2)
-        assert np.array_equal(g1.cpu().numpy(), g2) and np.array_equal(l1.cpu().numpy(), l2)
+        # same inputs; the FP64 sweep sums G with shared-memory atomics shared by warp pairs,
+        # so results may differ in the last bits between launches
+        assert np.allclose(r1.cpu().numpy(), r2, rtol=1e-12, atol=0)
+        assert np.allclose(g1.cpu().numpy(), g2, rtol=1e-12, atol=1e-14)
+        assert np.allclose(l1.cpu().numpy(), l2, rtol=1e-12, atol=1e-14)
         acc = (u[t] < r2 * r2).astype(np.uint8)
         a.accept(e, torch.tensor(acc, device="cuda"))
         b.accept_host(e, acc)

@@ -141,3 +141,55 @@ def test_null_arguments_are_rejected(lib):
 
 def test_graft_build_entry():
     __graft_entry__.build()
+
+
+def _describe(lib, problem):
+    s, keep = _struct(problem)
+    out = np.zeros(32, dtype=np.int64)
+    rc = lib.msd_describe(ctypes.byref(s), out.ctypes.data)
+    assert rc == 0, lib.msd_last_error(None).decode()
+    return out.reshape(2, 16)
+
+
+@pytest.mark.parametrize("label,kw", [("water", {}), ("medium", {"n_walkers": 2}),
+                                      ("large", {"n_walkers": 2, "n_det": 20000})])
+def test_device_layout_plan(lib, label, kw):
+    """The host-side plan of msd_init (string groups, dense singles, term lists), no GPU."""
+    p = wl.make_workload(label, **kw).problem
+    d = _describe(lib, p)
+    for s in range(2):
+        n, m = p.n_elec[s], p.n_orb[s] - p.n_elec[s]
+        hist = np.bincount(p.exc_orders(s), minlength=9)
+        dense = hist[1] > 0 and 4 * hist[1] >= n * m
+        assert d[s, 1] == int(dense)
+        goff = d[s, 5:15]
+        assert goff[0] == 0 and np.all(np.diff(goff) >= 0)
+        sizes = np.diff(goff)
+        assert sizes[0] == hist[0]
+        assert sizes[1] == (n * m if dense else hist[1])
+        assert np.array_equal(sizes[2:], hist[2:9])
+        assert d[s, 0] == goff[-1] == p.n_exc(s) - hist[1] + sizes[1]
+        assert d[s, 2] == int(np.nonzero(hist)[0].max())
+        assert d[s, 15] == p.n_det
+        rb = {1: 2, 2: 4, 3: 8, 4: 8}
+        want = 0
+        for k in range(2 if dense else 1, 9):
+            want = (want + 15) // 16 * 16 + int(hist[k]) * rb.get(k, 16)
+        assert d[s, 4] == (want + 15) // 16 * 16
+
+
+def test_device_layout_plan_edge_cases(lib):
+    # sparse singles (well under a quarter of the n m pairs) stay in per-excitation records
+    w = wl.custom_workload((11, 9), (25, 26), 700, wl.uniform_orders(1, 8), W=3, n_nuc=4, seed=11)
+    d = _describe(lib, w.problem)
+    assert d[0, 2] == 8
+    # one electron per spin, single determinant, no virtual orbitals
+    base = wl.make_workload("water", n_walkers=2).problem
+    B0 = (np.ascontiguousarray(base.B[0][:, :5]), np.ascontiguousarray(base.B[1][:, :5]))
+    single = wl.explicit_problem(base.nuc_xyz, base.bas_center, base.bas_lm, base.bas_alpha, B0, base.n_elec,
+                                 [((), ())], [((), ())], [0], [0], [1.0])
+    d = _describe(lib, single)
+    assert d[0, 0] == 1 and d[1, 0] == 1 and d[0, 15] == 1
+    w = wl.custom_workload((1, 1), (6, 4), 9, wl.uniform_orders(1, 2), W=1, n_nuc=2, seed=3)
+    d = _describe(lib, w.problem)
+    assert d[0, 1] == 1 and d[0, 0] == 1 + 5  # dense singles: one hole, five virtuals

@@ -2,10 +2,11 @@
 against exact rational determinants (no GPU needed).
 
 ``paper_1106_2456_gb300/csrc/msd_smalldet.cuh`` holds the code that the excitation-sweep
-kernel runs for every excitation of order k: det T_u, and the five bordered determinants
-det [[T_u, x_u], [-y^a_u^T, s^a]] sharing one pivoted LU of T_u.  Here it is compiled by g++
-through ``tests/native/smalldet_host.cpp`` and compared with the exact determinant of the
-same floating-point inputs (Python fractions).  The adversarial inputs give T a large
+kernel runs for every excitation of order k: det T_u and z = adj(T_u) x_u from one pivoted
+LU; every bordered determinant of a move is det [[T_u, x_u], [-y^T, s]] = det(T_u) s + y . z.
+Here it is compiled by g++ through ``tests/native/smalldet_host.cpp``; the bordered values
+it implies are compared with the exact determinant of the same floating-point inputs
+(Python fractions).  The adversarial inputs give T a large
 rank-1 component, as an ill-conditioned reference matrix A_0 does to T = A_0^{-1} Phi_virt;
 closed-form cofactor expansions lose up to 1e-4 relative accuracy there (k = 3), which this
 test would catch.
@@ -40,8 +41,10 @@ def lib():
     L.sd_det_f64.argtypes = [ci, vp, ci, vp, vp]
     L.sd_det_f32.restype = ctypes.c_float
     L.sd_det_f32.argtypes = [ci, vp, ci, vp, vp]
-    L.sd_bordered_f64.argtypes = [ci, vp, ci, vp, vp, ci, vp, vp, vp, vp]
-    L.sd_bordered_f32.argtypes = [ci, vp, ci, vp, vp, ci, vp, vp, vp, vp]
+    L.sd_adj_f64.restype = ctypes.c_double
+    L.sd_adj_f64.argtypes = [ci, vp, ci, vp, vp, vp, vp]
+    L.sd_adj_f32.restype = ctypes.c_float
+    L.sd_adj_f32.argtypes = [ci, vp, ci, vp, vp, vp, vp]
     return L
 
 
@@ -77,10 +80,11 @@ def case(rng, K, blowup, dtype):
 
 
 def run(lib, K, T, x, y, s, h, p, m, f32):
-    d = np.zeros(5, dtype=np.float32 if f32 else np.float64)
-    fn = lib.sd_bordered_f32 if f32 else lib.sd_bordered_f64
-    fn(K, T.ctypes.data, m, x.ctypes.data, y.ctypes.data, m, s.ctypes.data, h.ctypes.data, p.ctypes.data,
-       d.ctypes.data)
+    """Bordered determinants det(T_u) s^a + y^a . z from the library's (det, z), and det T_u."""
+    z = np.zeros(K, dtype=np.float32 if f32 else np.float64)
+    fn = lib.sd_adj_f32 if f32 else lib.sd_adj_f64
+    det = fn(K, T.ctypes.data, m, x.ctypes.data, h.ctypes.data, p.ctypes.data, z.ctypes.data)
+    d = np.array([det * s[a] + np.dot(y[a, p], z) for a in range(5)], dtype=z.dtype)
     dt = (lib.sd_det_f32 if f32 else lib.sd_det_f64)(K, T.ctypes.data, m, h.ctypes.data, p.ctypes.data)
     return d, dt
 
