@@ -6,10 +6,14 @@
 //   small_det : det T_u                               (= det A_u / det A_0, Section III)
 //   adj_solve : det T_u and z = adj(T_u) x_u          (the two ingredients of every bordered
 //               determinant det [[T_u, x_u], [-y^T, s]] = det(T_u) s + y . z, Section IV-A/C)
-// Both use an LU with partial pivoting held in registers.  Closed-form cofactor expansions
-// are not used for k >= 2: when A_0 is nearly singular, T = A_0^{-1} Phi_virt carries a large
-// rank-1 component and products of its entries cancel catastrophically, while the pivoted
-// elimination removes that component in its first step.
+// Both eliminate the first k-2 columns by LU with partial pivoting held in registers and
+// finish the remaining 2 x 2 Schur complement in closed form, each 2 x 2 determinant
+// a d - b c evaluated with one FMA-based error correction (Kahan's method), so it is accurate
+// to a few units in the last place whatever the cancellation.  Plain closed-form cofactor
+// expansions are not used for k >= 3: when A_0 is nearly singular, T = A_0^{-1} Phi_virt
+// carries a large rank-1 component and products of its entries cancel catastrophically,
+// while the pivoted elimination removes that component in its first step.  The only division
+// is one reciprocal per eliminated column (none for k <= 2).
 #pragma once
 
 #include <cmath>
@@ -45,15 +49,27 @@ MSD_HD float recip(float x) {
 #endif
 }
 
-// In-register LU with partial pivoting of the K x K block M; the right-hand side b is
-// permuted and eliminated alongside.  On return M holds U above the diagonal and 1/u_kk on it;
-// the return value is det M; `singular` is set if a pivot is exactly zero.
-template <int K, typename TT>
-MSD_HD TT lu_inplace(TT (&M)[K][K], TT (&b)[K], bool& singular) {
-    TT det = TT(1);
+// a b - c d with the rounding error of c d added back (Kahan's 2 x 2 determinant): the result
+// is within about 2 ulp of the exact value even when the two products nearly cancel.
+template <typename T>
+MSD_HD T dop(T a, T b, T c, T d) {
+    const T w = c * d;
+    const T e = fma(-c, d, w);
+    const T f = fma(a, b, -w);
+    return f + e;
+}
+
+// S steps of LU with partial pivoting on the K x K block M, the right-hand side b permuted and
+// eliminated alongside.  On return rows/columns < S hold U with 1/u_kk on the diagonal, the
+// trailing (K-S) x (K-S) block holds the Schur complement, and the return value is
+// sign(P) * prod u_kk.  `singular` is set if a pivot is exactly zero (the column below the
+// diagonal is then zero and T_u is singular).
+template <int K, int S, typename TT>
+MSD_HD TT lu_steps(TT (&M)[K][K], TT (&b)[K], bool& singular) {
+    TT dp = TT(1);
     singular = false;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < S; ++k) {
         int piv = k;
         TT best = tabs(M[k][k]);
 #pragma unroll
@@ -78,7 +94,7 @@ MSD_HD TT lu_inplace(TT (&M)[K][K], TT (&b)[K], bool& singular) {
             b[r] = sw ? x : y;
         }
         const TT pv = M[k][k];
-        det = (piv != k) ? -det * pv : det * pv;
+        dp = (piv != k) ? -dp * pv : dp * pv;
         singular |= (pv == TT(0));
         const TT ip = recip(pv);
 #pragma unroll
@@ -90,7 +106,7 @@ MSD_HD TT lu_inplace(TT (&M)[K][K], TT (&b)[K], bool& singular) {
         }
         M[k][k] = ip;
     }
-    return det;
+    return dp;
 }
 
 // det T_u.
@@ -98,6 +114,8 @@ template <int K, typename TT>
 MSD_HD TT small_det(const TT* Ts, int ld, const int (&h)[K], const int (&p)[K]) {
     if constexpr (K == 1) {
         return Ts[h[0] * ld + p[0]];
+    } else if constexpr (K == 2) {
+        return dop(Ts[h[0] * ld + p[0]], Ts[h[1] * ld + p[1]], Ts[h[0] * ld + p[1]], Ts[h[1] * ld + p[0]]);
     } else {
         TT M[K][K], b[K];
 #pragma unroll
@@ -107,8 +125,9 @@ MSD_HD TT small_det(const TT* Ts, int ld, const int (&h)[K], const int (&p)[K]) 
             for (int l = 0; l < K; ++l) M[q][l] = Ts[h[q] * ld + p[l]];
         }
         bool singular;
-        const TT det = lu_inplace<K, TT>(M, b, singular);
-        return singular ? TT(0) : det;
+        const TT dp = lu_steps<K, K - 2, TT>(M, b, singular);
+        constexpr int a = K - 2, c = K - 1;
+        return singular ? TT(0) : dp * dop(M[a][a], M[c][c], M[a][c], M[c][a]);
     }
 }
 
@@ -148,6 +167,9 @@ MSD_HD_NOINLINE void adj_cramer(int K, const TT* Ts, int ld, const TT* xs, const
 }
 
 // det T_u and z = adj(T_u) x_u = det(T_u) T_u^{-1} x_u, z indexed by particle slot l.
+// With U_11 (pivots u_jj), U_12, Schur block S and b' = (b'_1, b'_2) after the first K-2
+// elimination steps: z_2 = sign(P) prod u_jj adj(S) b'_2 and z_1 = U_11^{-1}(det b'_1 - U_12 z_2),
+// which needs no division beyond the stored 1/u_jj and stays valid when det S = 0.
 template <int K, typename TT>
 MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], const int (&p)[K], TT& det,
                       TT (&z)[K]) {
@@ -163,7 +185,7 @@ MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], con
             b[q] = xs[h[q]];
         }
         bool singular;
-        det = lu_inplace<K, TT>(M, b, singular);
+        const TT dp = lu_steps<K, K - 2, TT>(M, b, singular);
         if (singular) {
             int hh[MSD_MAX_ORDER], pp[MSD_MAX_ORDER];
             TT zz[MSD_MAX_ORDER];
@@ -178,16 +200,17 @@ MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], con
             for (int q = 0; q < K; ++q) z[q] = zz[q];
             return;
         }
-        // back substitution U z' = b', then z = det z'
+        constexpr int a = K - 2, c = K - 1;
+        det = dp * dop(M[a][a], M[c][c], M[a][c], M[c][a]);
+        z[a] = dp * dop(M[c][c], b[a], M[a][c], b[c]);
+        z[c] = dp * dop(M[a][a], b[c], M[c][a], b[a]);
 #pragma unroll
-        for (int q = K - 1; q >= 0; --q) {
-            TT acc = b[q];
+        for (int q = K - 3; q >= 0; --q) {
+            TT acc = det * b[q];
 #pragma unroll
             for (int j = q + 1; j < K; ++j) acc = fma(-M[q][j], z[j], acc);
             z[q] = acc * M[q][q];
         }
-#pragma unroll
-        for (int q = 0; q < K; ++q) z[q] *= det;
     }
 }
 

@@ -2,8 +2,10 @@
 against exact rational determinants (no GPU needed).
 
 ``paper_1106_2456_gb300/csrc/msd_smalldet.cuh`` holds the code that the excitation-sweep
-kernel runs for every excitation of order k: det T_u and z = adj(T_u) x_u from one pivoted
-LU; every bordered determinant of a move is det [[T_u, x_u], [-y^T, s]] = det(T_u) s + y . z.
+kernel runs for every excitation of order k: det T_u and z = adj(T_u) x_u from a pivoted LU
+of the first k-2 columns and a closed-form 2 x 2 Schur block (FMA-corrected 2 x 2
+determinants); every bordered determinant of a move is det [[T_u, x_u], [-y^T, s]] =
+det(T_u) s + y . z.
 Here it is compiled by g++ through ``tests/native/smalldet_host.cpp``; the bordered values
 it implies are compared with the exact determinant of the same floating-point inputs
 (Python fractions).  The adversarial inputs give T a large
