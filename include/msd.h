@@ -97,9 +97,9 @@ typedef struct {
 typedef struct msd_ctx msd_ctx;
 
 /* Create a context for n_systems problems (only n_systems == 1 is accepted by this
- * build; batched uneven systems return MSD_ERR_ARG).  Validates every array, reorders
- * the excitation strings by order (and lexicographically within an order) for the
- * device, and allocates all per-walker state.  *out is NULL on failure. */
+ * build; batched uneven systems return MSD_ERR_ARG).  Validates every array, groups the
+ * excitation strings by order and packs each order into batches of 32 for the device
+ * (msd_describe_records), and allocates all per-walker state.  *out is NULL on failure. */
 msd_status msd_init(const msd_problem* prob, int32_t n_systems, msd_ctx** out);
 
 /* Validate a problem and report, without any CUDA call, the device layout msd_init would
@@ -108,6 +108,18 @@ msd_status msd_init(const msd_problem* prob, int32_t n_systems, msd_ctx** out);
  * than a threshold number of terms, [4] = bytes of excitation records, [5 .. 14] = first
  * internal index of each order 0..8 and the end, [15] = terms referenced.  out has 32 entries. */
 msd_status msd_describe(const msd_problem* prob, int64_t* out);
+
+/* The device excitation records of spin `spin` that msd_init would build, without any CUDA
+ * call.  Records of order k >= 1 (k = 1 only when the singles are not a dense block) start at
+ * byte out_off[k] (out_off has MSD_MAX_ORDER + 2 entries; out_off[MSD_MAX_ORDER + 1] = total
+ * bytes) and come in batches of 32, one record per internal string: k hole bytes, then k
+ * particle bytes, padded to 2, 4, 8 or 16 bytes (orders 1, 2, 3-4, 5-8).  A record whose
+ * first byte is 0xFF is an empty slot.  Within a batch the particles in any one slot have
+ * distinct residues mod 32; within a record holes and particles may be permuted with equal
+ * parity (Section III: det T_u is unchanged).  out may be NULL to query the size; otherwise
+ * it must hold `cap` bytes and receives min(cap, total) bytes; *bytes = total. */
+msd_status msd_describe_records(const msd_problem* prob, int32_t spin, uint8_t* out, int64_t cap, int64_t* out_off,
+                                int64_t* bytes);
 
 /* Set the walker positions R_dev [W][n_tot][3] and build the state from scratch:
  * orbitals, LU of A_0 (A_0^{-1}, log|det A_0|, sign), T = A_0^{-1} Phi_virt and the CI

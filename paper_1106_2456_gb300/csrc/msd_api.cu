@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <array>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -212,7 +214,8 @@ msd_status validate(const msd_problem* p) {
         const int n = p->n_elec[s], m = p->n_orb[s] - p->n_elec[s];
         const size_t need = ratio_smem_bytes(mixed, n, m, NCH);
         const size_t inv = (size_t)n * (n + 1) * 8 + (size_t)n * 12 + 16;
-        if (need > 220 * 1024 || inv > 220 * 1024)
+        // (also bounds n below 255, so hole byte 0xFF can mark an empty record slot)
+        if (need > 220 * 1024 || inv > 220 * 1024 || n >= (int)kEmptyRecord)
             return fail(nullptr, MSD_ERR_ARG,
                         "spin %d: per-walker table (%d x %d) does not fit in one SM's shared memory", s, n, m);
     }
@@ -221,6 +224,90 @@ msd_status validate(const msd_problem* p) {
 
 // Build device strings of spin s, grouped by order and sorted within each order.  Singles
 // become a dense n x m block of internal indices when at least a quarter of them are present.
+// Packs the strings of order k into warp batches of kBatch internal slots (Section III
+// excitations, one per lane of a warp).  Within a batch the particle in slot l of every
+// excitation has a distinct residue mod 32, so the lanes' scatter-adds into G never collide and
+// their table reads T[h][p] (row stride a multiple of 32) fall in distinct shared-memory banks.
+// The particles of an excitation may sit in any slot order; its holes are permuted with the same
+// parity, which leaves det T_u and the per-particle entries of adj(T_u) x_u unchanged.  Each
+// string goes to the first of the kWindow most recently opened batches where a slot assignment
+// exists (a bipartite matching of its particles to free slots), else opens a new batch; unused
+// slots hold kEmptyRecord records.
+// Returns the number of internal slots used (a multiple of kBatch).
+int pack_group(SpinConst& S, const msd_problem* p, int s, int k, const int* members, int count, int idx0,
+               std::vector<uint8_t>& rec) {
+    constexpr int kWindow = 512;
+    const int32_t* off = p->exc_off[s];
+    struct Batch {
+        uint32_t used[MAXK];
+        int cnt;
+    };
+    std::vector<Batch> batches;
+    std::vector<int> batch_of(count), lane_of(count);
+    std::vector<std::array<int8_t, MAXK>> slot_of(count);
+    int first_open = 0;
+    int res[MAXK], owner[MAXK], slot[MAXK];
+    // augmenting-path search: particle i takes a slot whose residue bit is free
+    std::function<bool(const Batch&, int, unsigned&)> augment = [&](const Batch& b, int i, unsigned& seen) {
+        for (int l = 0; l < k; ++l) {
+            if (((b.used[l] >> res[i]) & 1u) || ((seen >> l) & 1u)) continue;
+            seen |= 1u << l;
+            if (owner[l] < 0 || augment(b, owner[l], seen)) {
+                owner[l] = i;
+                slot[i] = l;
+                return true;
+            }
+        }
+        return false;
+    };
+    auto fits = [&](const Batch& b) {
+        for (int l = 0; l < k; ++l) owner[l] = -1;
+        for (int i = 0; i < k; ++i) {
+            unsigned seen = 0;
+            if (!augment(b, i, seen)) return false;
+        }
+        return true;
+    };
+    for (int e = 0; e < count; ++e) {
+        const int u = members[e];
+        for (int i = 0; i < k; ++i) res[i] = p->exc_parts[s][off[u] + i] & 31;
+        int bi = -1;
+        const int last = (int)batches.size();
+        for (int b = std::max(first_open, last - kWindow); b < last && bi < 0; ++b)
+            if (batches[b].cnt < kBatch && fits(batches[b])) bi = b;
+        if (bi < 0) {
+            batches.push_back(Batch{});
+            bi = (int)batches.size() - 1;
+            for (int i = 0; i < k; ++i) slot[i] = i;
+        }
+        Batch& b = batches[bi];
+        for (int i = 0; i < k; ++i) {
+            b.used[slot[i]] |= 1u << res[i];
+            slot_of[e][i] = (int8_t)slot[i];
+        }
+        batch_of[e] = bi;
+        lane_of[e] = b.cnt++;
+        while (first_open < (int)batches.size() && batches[first_open].cnt == kBatch) ++first_open;
+    }
+    const int rb = rec_bytes(k);
+    const size_t base = rec.size();
+    rec.resize(base + (size_t)batches.size() * kBatch * rb, kEmptyRecord);
+    for (int e = 0; e < count; ++e) {
+        const int u = members[e];
+        const int i_int = batch_of[e] * kBatch + lane_of[e];
+        S.internal_of[u] = idx0 + i_int;
+        uint8_t* r = rec.data() + base + (size_t)i_int * rb;
+        for (int q = 0; q < rb; ++q) r[q] = 0;
+        int inv = 0;  // parity of the particle placement
+        for (int i = 0; i < k; ++i)
+            for (int j = i + 1; j < k; ++j) inv += slot_of[e][i] > slot_of[e][j];
+        for (int q = 0; q < k; ++q) r[q] = p->exc_holes[s][off[u] + q];
+        if (inv & 1) std::swap(r[0], r[1]);  // odd placement (k >= 2): an odd hole permutation
+        for (int i = 0; i < k; ++i) r[k + slot_of[e][i]] = p->exc_parts[s][off[u] + i];
+    }
+    return (int)batches.size() * kBatch;
+}
+
 msd_status plan_strings(SpinConst& S, const msd_problem* p, int s) {
     const int ne = p->n_exc[s];
     const int32_t* off = p->exc_off[s];
@@ -250,44 +337,32 @@ msd_status plan_strings(SpinConst& S, const msd_problem* p, int s) {
     };
     std::stable_sort(order.begin(), order.end(), key_less);  // the reference (k = 0, index 0) stays first
     S.internal_of.assign(ne, -1);
+    std::vector<uint8_t> rec;
+    for (int k = 0; k <= MAXK + 1; ++k) S.g.roff[k] = 0;
     int idx = 0, pos = 0;
     for (int k = 0; k <= MAXK; ++k) {
         S.g.goff[k] = idx;
-        if (k == 1 && dense1) {
-            for (; pos < ne && order_of(order[pos]) == 1; ++pos) {
-                const int u = order[pos];
+        while (rec.size() % 16) rec.push_back(0);
+        S.g.roff[k] = (long long)rec.size();
+        const int first = pos;
+        while (pos < ne && order_of(order[pos]) == k) ++pos;
+        if (k == 0) {
+            for (int i = first; i < pos; ++i) S.internal_of[order[i]] = idx++;
+        } else if (k == 1 && dense1) {
+            for (int i = first; i < pos; ++i) {
+                const int u = order[i];
                 S.internal_of[u] = idx + p->exc_holes[s][off[u]] * S.m + p->exc_parts[s][off[u]];
             }
             idx += S.n * S.m;
-            continue;
+        } else if (pos > first) {
+            idx += pack_group(S, p, s, k, order.data() + first, pos - first, idx, rec);
         }
-        for (; pos < ne && order_of(order[pos]) == k; ++pos) S.internal_of[order[pos]] = idx++;
     }
+    while (rec.size() % 16) rec.push_back(0);
     S.g.goff[MAXK + 1] = idx;
     S.g.n_exc = idx;
     S.user_of.assign(idx, -1);
     for (int u = 0; u < ne; ++u) S.user_of[S.internal_of[u]] = u;
-    // records of the groups processed one excitation per thread
-    std::vector<uint8_t> rec;
-    for (int k = 0; k <= MAXK + 1; ++k) S.g.roff[k] = 0;
-    pos = 0;
-    for (int k = 1; k <= MAXK; ++k) {
-        while (rec.size() % 16) rec.push_back(0);
-        S.g.roff[k] = (long long)rec.size();
-        if (k == 1 && dense1) continue;
-        const int rb = rec_bytes(k);
-        for (int i = 0; i < ne; ++i) {
-            const int u = order[i];
-            if (order_of(u) != k) continue;
-            const size_t base = rec.size();
-            rec.resize(base + rb, 0);
-            for (int q = 0; q < k; ++q) {
-                rec[base + q] = p->exc_holes[s][off[u] + q];
-                rec[base + k + q] = p->exc_parts[s][off[u] + q];
-            }
-        }
-    }
-    while (rec.size() % 16) rec.push_back(0);
     S.h_rec.swap(rec);
     S.g.rec = nullptr;
     return MSD_OK;
@@ -522,6 +597,21 @@ msd_status msd_describe(const msd_problem* p, int64_t* out) {
         for (int k = 0; k <= MAXK + 1; ++k) o[5 + k] = sp[s].g.goff[k];
         o[15] = (int64_t)sp[s].h_toff.back();
     }
+    return MSD_OK;
+}
+
+msd_status msd_describe_records(const msd_problem* p, int32_t spin, uint8_t* out, int64_t cap, int64_t* out_off,
+                                int64_t* bytes) {
+    g_init_error.clear();
+    if (!bytes || !out_off || spin < 0 || spin > 1 || cap < 0) return fail(nullptr, MSD_ERR_ARG, "invalid argument");
+    TRY(validate(p));
+    SpinConst sp[2];
+    TRY(plan_problem(sp, p));
+    const SpinConst& S = sp[spin];
+    for (int k = 0; k <= MAXK; ++k) out_off[k] = S.g.roff[k];
+    out_off[MAXK + 1] = (int64_t)S.h_rec.size();
+    *bytes = (int64_t)S.h_rec.size();
+    if (out) std::memcpy(out, S.h_rec.data(), (size_t)std::min<int64_t>(cap, *bytes));
     return MSD_OK;
 }
 

@@ -23,11 +23,15 @@ __host__ __device__ constexpr int rec_bytes(int k) {
 }
 
 // Excitation strings of one spin on the device, grouped by order.  Internal index i of
-// order k lies in [goff[k], goff[k+1]); group 0 holds the reference.  Group k's records
-// start at byte roff[k] of rec.  Within a group strings are sorted lexicographically by
-// (holes, particles) so consecutive threads share table rows.  With dense1 set the singles
-// occupy a dense n x m block (index goff[1] + h m + p; absent singles carry C = 0) and have
-// no records.
+// order k lies in [goff[k], goff[k+1]); group 0 holds the reference.  Group k >= 1 (unless
+// dense) is a whole number of warp batches of kBatch records starting at byte roff[k] of rec;
+// the lane-l record of a batch is the string that lane l handles, and no two records of a batch
+// share the residue mod 32 of the particle in any one slot.  Unused slots hold records filled
+// with kEmptyRecord bytes and carry C = 0; their first hole byte 0xFF is no valid hole (a spin
+// with 255 or more electrons is rejected: its A_0^{-1} would not fit in shared memory).  With dense1 set the singles occupy a
+// dense n x m block (index goff[1] + h m + p; absent singles carry C = 0) and have no records.
+constexpr int kBatch = 32;
+constexpr uint8_t kEmptyRecord = 0xFF;
 struct ExcDev {
     int n_exc = 0;
     int kmax = 0;

@@ -389,7 +389,7 @@ __device__ __forceinline__ void det_group(const ExcDev& g, const TT* Ts, int ld,
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         int h[K], p[K];
         load_rec<K>(rec, j - j0, h, p);
-        tw[j] = small_det<K, TT>(Ts, ld, h, p);
+        tw[j] = h[0] == kEmptyRecord ? TT(0) : small_det<K, TT>(Ts, ld, h, p);
     }
 }
 
@@ -488,38 +488,40 @@ __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int l
                                             const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int base) {
     const int j0 = g.goff[K], j1 = g.goff[K + 1];
     const uint8_t* rec = g.rec + g.roff[K];
-    const int step = blockDim.x;
-    TT* Gmine = Gw + ((threadIdx.x >> 5) % NGW) * ld;
-    // Threads stride over the concatenation of all groups from `base` on, so the remainder of
-    // each group lands on different threads and the per-thread work stays balanced.
-    const int rot = (j0 - base) % step;
-    const int first = (int(threadIdx.x) - rot + step) % step;
-    // two iterations of record and C loads in flight ahead of the arithmetic
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    TT* Gmine = Gw + (warp % NGW) * ld;
+    // Warps take the group's batches of 32 strings round-robin, numbered across all groups from
+    // `base` on, so the batches left over at the end of a group fall on different warps.
+    const int nb = (j1 - j0) / kBatch;
+    int b = (warp - ((j0 - base) / kBatch) % nw + nw) % nw;
+    // two batches of record and C loads in flight ahead of the arithmetic
     using Raw = typename RecRaw<K>::type;
-    int j = j0 + first;
     Raw r0{}, r1{};
     TT c0 = TT(0), c1 = TT(0);
-    if (j < j1) { r0 = load_raw<K>(rec, j - j0); c0 = __ldcs(Cw + j); }
-    if (j + step < j1) { r1 = load_raw<K>(rec, j + step - j0); c1 = __ldcs(Cw + j + step); }
-    for (; j < j1; j += step) {
+    if (b < nb) { r0 = load_raw<K>(rec, b * kBatch + lane); c0 = __ldcs(Cw + j0 + b * kBatch + lane); }
+    if (b + nw < nb) { r1 = load_raw<K>(rec, (b + nw) * kBatch + lane); c1 = __ldcs(Cw + j0 + (b + nw) * kBatch + lane); }
+    for (; b < nb; b += nw) {
         const Raw rc = r0;
         const TT cu = c0;
         r0 = r1;
         c0 = c1;
-        const int jn = j + 2 * step;
-        if (jn < j1) { r1 = load_raw<K>(rec, jn - j0); c1 = __ldcs(Cw + jn); }
+        const int bn = b + 2 * nw;
+        if (bn < nb) { r1 = load_raw<K>(rec, bn * kBatch + lane); c1 = __ldcs(Cw + j0 + bn * kBatch + lane); }
         int h[K], p[K];
         decode_rec<K>(rc, h, p);
-        TT det, z[K];
-        adj_solve<K, TT>(Ts, ld, xs, h, p, det, z);
-        sacc.add(0, cu * det);
+        if (h[0] != kEmptyRecord) {
+            TT det, z[K];
+            adj_solve<K, TT>(Ts, ld, xs, h, p, det, z);
+            sacc.add(0, cu * det);
+            // the batch's particles in any one slot lie in distinct banks: no conflicts
 #pragma unroll
-        for (int l = 0; l < K; ++l) atomicAdd(Gmine + p[l], cu * z[l]);
+            for (int l = 0; l < K; ++l) atomicAdd(Gmine + p[l], cu * z[l]);
+        }
     }
 }
 
 struct RatioSmem {
-    size_t ts, xd, xs, ph, g1, gw, red, total;
+    size_t ts, xd, xs, ph, g1, gw, tg, red, total;
 };
 
 __host__ __device__ inline RatioSmem ratio_layout(int n, int m, int nch, int tt_bytes, int to_bytes, int ngw) {
@@ -532,21 +534,51 @@ __host__ __device__ inline RatioSmem ratio_layout(int n, int m, int nch, int tt_
     L.ph = up(L.xs + (size_t)n * tt_bytes);
     L.g1 = up(L.ph + (size_t)nch * n * to_bytes);
     L.gw = up(L.g1 + mm * tt_bytes);
-    L.red = up(L.gw + (size_t)ngw * mm * tt_bytes);
+    L.tg = up(L.gw + (size_t)ngw * mm * tt_bytes);
+    L.red = up(L.tg + (size_t)n * tt_bytes);
     L.total = up(L.red + (size_t)32 * (NCH + 1) * 8);
     return L;
 }
 
-// Copies of G per block: one per warp in FP32 (deterministic), one per warp pair in FP64 so two
-// blocks of 256 threads fit an SM.
+// Copies of G per block: one per warp in FP32, one per warp pair in FP64 so two blocks of 256
+// threads fit an SM.
 template <typename TT>
 __host__ __device__ constexpr int ratio_ngw() {
     return sizeof(TT) == 4 ? kWarps : kWarps / 2;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Asynchronous global -> shared copy of `bytes` (a multiple of 4) by the whole block
+// (cp.async, completion awaited with cp_async_wait_all); 16-byte pieces when both ends allow.
+__device__ __forceinline__ void cp_async_block(void* dst, const void* src, size_t bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const char* sp = static_cast<const char*>(src);
+    if (((reinterpret_cast<uintptr_t>(src) | d) & 15) == 0 && (bytes & 15) == 0) {
+        for (size_t o = size_t(threadIdx.x) * 16; o < bytes; o += size_t(blockDim.x) * 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + (uint32_t)o), "l"(sp + o) : "memory");
+    } else {
+        for (size_t o = size_t(threadIdx.x) * 4; o < bytes; o += size_t(blockDim.x) * 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + (uint32_t)o), "l"(sp + o) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 #ifndef MSD_RATIO_F32_BLOCKS
 #define MSD_RATIO_F32_BLOCKS 3
 #endif
+// One block per walker.  The table is copied to shared memory asynchronously while the block
+// loads x and phi(r') and forms rho and s^a; the sweep then builds S_T and G; the epilogue needs
+// one table-vector product TG = T G:
+//   sum_p y^a[p] G[p] = phi^a_virt . G - phi^a_occ . TG,   y^a = phi^a_virt - T^T phi^a_occ,
+// and y^0 itself only when the proposal is kept for msd_accept.  FP32 tables reduce across a
+// warp in FP32 and across warps in FP64.
 template <typename TO, typename TT, int NC>
 __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
     k_ratio(RatioArgs a, int* __restrict__ status) {
@@ -560,10 +592,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
     TO* ph = reinterpret_cast<TO*>(smem + L.ph);
     TT* G1 = reinterpret_cast<TT*>(smem + L.g1);
     TT* Gw = reinterpret_cast<TT*>(smem + L.gw);
+    TT* TG = reinterpret_cast<TT*>(smem + L.tg);
     double* red = reinterpret_cast<double*>(smem + L.red);
     __shared__ double s_s[NC];
 
     const int w = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (m > 0) cp_async_block(Ts, static_cast<const TT*>(a.T) + (long long)w * n * m, (size_t)n * m * sizeof(TT));
     const TO* phw = static_cast<const TO*>(a.phi) + (long long)w * NC * N;
     const double* Aw = a.Ainv + (long long)w * n * n;
     for (int c = tid; c < n; c += bd) {
@@ -577,18 +612,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
     }
     for (int q = tid; q < (m > 0 ? m : 1); q += bd) G1[q] = TT(0);
     for (int q = tid; q < NGW * (m > 0 ? m : 1); q += bd) Gw[q] = TT(0);
-    copy_to_smem(Ts, static_cast<const TT*>(a.T) + (long long)w * n * m, (long long)n * m);
     __syncthreads();
     // A2: rho = phi_occ(r') . x and s^a = d^a phi_occ(r') . x (FP64)
-    {
-        const int warp = tid >> 5, lane = tid & 31;
-        if (warp < NC) {
-            double acc = 0.0;
-            for (int c = lane; c < n; c += 32) acc = fma(double(ph[warp * n + c]), xd[c], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) s_s[warp] = acc;
-        }
+    if (warp < NC) {
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc = fma(double(ph[warp * n + c]), xd[c], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) s_s[warp] = acc;
     }
+    cp_async_wait_all();
+    __syncthreads();
     // A4: S_T and G over every excitation
     Accum<TT, 1> sacc;
     sacc.zero();
@@ -596,17 +629,17 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
     for (int j = a.g.goff[0] + tid; j < a.g.goff[1]; j += bd) sacc.add(0, Cw[j]);
     if (a.g.dense1) {
         // column p of the dense singles block: G1[p] = sum_h C1[h][p] x[h], S_T += C1[h][p] T[h][p];
-        // eight rows per round so eight loads of the C stream are in flight per thread
+        // sixteen rows per round so sixteen loads of the C stream are in flight per thread
         const TT* C1 = Cw + a.g.goff[1];
         for (int pv = tid; pv < m; pv += bd) {
             TT g = TT(0), st = TT(0);
             int h = 0;
-            for (; h + 8 <= n; h += 8) {
-                TT c[8];
+            for (; h + 16 <= n; h += 16) {
+                TT c[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) c[q] = __ldcs(C1 + (h + q) * m + pv);
+                for (int q = 0; q < 16; ++q) c[q] = __ldcs(C1 + (h + q) * m + pv);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < 16; ++q) {
                     g = fma(c[q], xs[h + q], g);
                     st = fma(c[q], Ts[(h + q) * m + pv], st);
                 }
@@ -634,30 +667,64 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
         }
     }
     __syncthreads();
-    // A3 + A5: y^a[p] = d^a phi_virt(r')[p] - sum_c T[c][p] d^a phi_occ(r')[c], contracted with G
-    double v[NC + 1];
-#pragma unroll
-    for (int al = 0; al < NC; ++al) v[al] = 0.0;
-    v[NC] = sacc.get(0);
+    // G = G1 + the per-warp copies, kept in G1
     for (int pv = tid; pv < m; pv += bd) {
         TT gp = G1[pv];
 #pragma unroll
         for (int q = 0; q < NGW; ++q) gp += Gw[q * m + pv];
-#pragma unroll
-        for (int al = 0; al < NC; ++al) {
-            TT y = TT(phw[al * N + n + pv]);
-            const TO* pa = ph + al * n;
-            for (int c = 0; c < n; ++c) y = fma(-Ts[c * m + pv], TT(pa[c]), y);
-            if (al == 0 && a.y0) static_cast<TT*>(a.y0)[(long long)w * m + pv] = y;
-            v[al] = fma(double(y), double(gp), v[al]);
+        G1[pv] = gp;
+    }
+    __syncthreads();
+    // TG[c] = sum_p T[c][p] G[p], one warp per row
+    for (int c = warp; c < n; c += bd >> 5) {
+        TT acc = TT(0);
+        for (int pv = lane; pv < m; pv += 32) acc = fma(Ts[c * m + pv], G1[pv], acc);
+        acc = warp_sum_t(acc);
+        if (lane == 0) TG[c] = acc;
+    }
+    // A3 (kept for msd_accept): y^0[p] = phi_virt(r')[p] - sum_c T[c][p] phi_occ(r')[c]
+    if (a.y0) {
+        TT* yw = static_cast<TT*>(a.y0) + (long long)w * m;
+        for (int pv = tid; pv < m; pv += bd) {
+            TT y = TT(phw[n + pv]);
+            for (int c = 0; c < n; ++c) y = fma(-Ts[c * m + pv], TT(ph[c]), y);
+            yw[pv] = y;
         }
     }
-    block_sum<NC + 1>(v, red);
+    __syncthreads();
+    // A5: sum_p y^a[p] G[p] per channel, and S_T
+    TT v[NC + 1];
+#pragma unroll
+    for (int al = 0; al < NC; ++al) v[al] = TT(0);
+    v[NC] = TT(sacc.get(0));
+    for (int pv = tid; pv < m; pv += bd) {
+        const TT gp = G1[pv];
+#pragma unroll
+        for (int al = 0; al < NC; ++al) v[al] = fma(TT(phw[al * N + n + pv]), gp, v[al]);
+    }
+    for (int c = tid; c < n; c += bd) {
+        const TT tg = TG[c];
+#pragma unroll
+        for (int al = 0; al < NC; ++al) v[al] = fma(-TT(ph[al * n + c]), tg, v[al]);
+    }
+#pragma unroll
+    for (int i = 0; i <= NC; ++i) v[i] = warp_sum_t(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i <= NC; ++i) red[warp * (NC + 1) + i] = double(v[i]);
+    __syncthreads();
     if (tid == 0) {
-        const double ST = v[NC];
+        double tot[NC + 1];
+#pragma unroll
+        for (int i = 0; i <= NC; ++i) {
+            double t = 0.0;
+            for (int q = 0; q < (bd >> 5); ++q) t += red[q * (NC + 1) + i];
+            tot[i] = t;
+        }
+        const double ST = tot[NC];
         double num[NC];
 #pragma unroll
-        for (int al = 0; al < NC; ++al) num[al] = fma(s_s[al], ST, v[al]);
+        for (int al = 0; al < NC; ++al) num[al] = fma(s_s[al], ST, tot[al]);
         const double ratio = num[0] / a.S[w];
         a.ratio[(long long)w * a.rs] = ratio;
         if constexpr (NC == 5) {
@@ -700,15 +767,18 @@ __global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict
         v[r] = acc - (r == a.row ? 1.0 : 0.0);
     }
     __syncthreads();
-    for (long long idx = tid; idx < (long long)n * n; idx += bd) {
-        const int c = int(idx / n), r = int(idx - (long long)c * n);
-        Aw[idx] = fma(-xr[c], v[r], Aw[idx]);
+    const int lane = tid & 31, nw = bd >> 5;
+    for (int c = tid >> 5; c < n; c += nw) {
+        double* row = Aw + (long long)c * n;
+        const double xc = xr[c];
+        for (int r = lane; r < n; r += 32) row[r] = fma(-xc, v[r], row[r]);
     }
     TT* Tw = static_cast<TT*>(a.T) + (long long)w * n * m;
     const TT* yw = static_cast<const TT*>(a.y0) + (long long)w * m;
-    for (long long idx = tid; idx < (long long)n * m; idx += bd) {
-        const int c = int(idx / m), av = int(idx - (long long)c * m);
-        Tw[idx] = fma(TT(xr[c]), yw[av], Tw[idx]);
+    for (int c = tid >> 5; c < n; c += nw) {
+        TT* row = Tw + (long long)c * m;
+        const TT xc = TT(xr[c]);
+        for (int av = lane; av < m; av += 32) row[av] = fma(xc, yw[av], row[av]);
     }
     if (tid == 0) {
         if (!(rho != 0.0) || !isfinite(rho)) atomicOr(status, ST_SINGULAR);

@@ -80,6 +80,7 @@ def load_library():
     sig = {
         "msd_init": ([vp, i32, vp], i32),
         "msd_describe": ([vp, vp], i32),
+        "msd_describe_records": ([vp, i32, vp, i64, vp, vp], i32),
         "msd_set_positions": ([vp, vp], i32),
         "msd_ratio": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_accept": ([vp, i32, vp], i32),

@@ -134,7 +134,10 @@ def test_grad_lap_and_eval_batch_at_current_positions():
         assert rel_err(g_all[:, e], ref["grad"], ref["absum"][:, 1:4]).max() <= FP64_TOL
         assert rel_err(l_all[:, e], ref["lap"], ref["absum"][:, 4]).max() <= FP64_TOL
         g1, l1 = ctx.grad_lap(e)
-        assert np.array_equal(g1.cpu().numpy(), g_all[:, e]) and np.array_equal(l1.cpu().numpy(), l_all[:, e])
+        # the FP64 sweep sums G with shared-memory atomics shared by warp pairs, so two launches
+        # may differ in the last bits
+        assert np.allclose(g1.cpu().numpy(), g_all[:, e], rtol=1e-12, atol=1e-14)
+        assert np.allclose(l1.cpu().numpy(), l_all[:, e], rtol=1e-12, atol=1e-14)
     # from-scratch evaluation at other positions leaves the walker state alone
     R2 = R + 0.05
     la, sg, g, l = ctx.eval_batch(R2, with_grad=True)

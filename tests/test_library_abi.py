@@ -166,16 +166,64 @@ def test_device_layout_plan(lib, label, kw):
         assert goff[0] == 0 and np.all(np.diff(goff) >= 0)
         sizes = np.diff(goff)
         assert sizes[0] == hist[0]
-        assert sizes[1] == (n * m if dense else hist[1])
-        assert np.array_equal(sizes[2:], hist[2:9])
-        assert d[s, 0] == goff[-1] == p.n_exc(s) - hist[1] + sizes[1]
+        if dense:
+            assert sizes[1] == n * m
+        for k in range(2 if dense else 1, 9):
+            assert sizes[k] % 32 == 0 and hist[k] <= sizes[k] and (sizes[k] > 0) == (hist[k] > 0)
+        assert d[s, 0] == goff[-1]
         assert d[s, 2] == int(np.nonzero(hist)[0].max())
         assert d[s, 15] == p.n_det
         rb = {1: 2, 2: 4, 3: 8, 4: 8}
         want = 0
         for k in range(2 if dense else 1, 9):
-            want = (want + 15) // 16 * 16 + int(hist[k]) * rb.get(k, 16)
+            want = (want + 15) // 16 * 16 + int(sizes[k]) * rb.get(k, 16)
         assert d[s, 4] == (want + 15) // 16 * 16
+        _check_records(lib, p, s, goff, dense)
+
+
+def _records(lib, problem, spin):
+    s, keep = _struct(problem)
+    off = np.zeros(10, dtype=np.int64)
+    nbytes = ctypes.c_int64()
+    assert lib.msd_describe_records(ctypes.byref(s), spin, None, 0, off.ctypes.data, ctypes.byref(nbytes)) == 0
+    out = np.zeros(max(nbytes.value, 1), dtype=np.uint8)
+    assert lib.msd_describe_records(ctypes.byref(s), spin, out.ctypes.data, out.size, off.ctypes.data,
+                                    ctypes.byref(nbytes)) == 0
+    return out, off
+
+
+def _perm_parity(a):
+    a = list(a)
+    inv = sum(1 for i in range(len(a)) for j in range(i + 1, len(a)) if a[i] > a[j])
+    return inv & 1
+
+
+def _check_records(lib, p, spin, goff, dense):
+    """Every string of order k appears once in its group's records, holes and particles
+    permuted with equal parity; slots of a batch hold distinct particle residues mod 32."""
+    out, off = _records(lib, p, spin)
+    rb = {1: 2, 2: 4, 3: 8, 4: 8}
+    offs = p.exc_off[spin]
+    for k in range(2 if dense else 1, 9):
+        size = goff[k + 1] - goff[k]
+        if size == 0:
+            continue
+        r = out[off[k]:off[k] + size * rb.get(k, 16)].reshape(size, rb.get(k, 16))
+        used = r[:, 0] != 0xFF
+        holes, parts = r[used, :k].astype(int), r[used, k:2 * k].astype(int)
+        # each string exactly once, with the same hole and particle sets
+        want = sorted((tuple(p.exc_holes[spin][offs[u]:offs[u + 1]]), tuple(p.exc_parts[spin][offs[u]:offs[u + 1]]))
+                      for u in range(p.n_exc(spin)) if offs[u + 1] - offs[u] == k)
+        got = sorted((tuple(sorted(h)), tuple(sorted(q))) for h, q in zip(holes, parts))
+        assert got == want
+        for h, q in zip(holes, parts):
+            assert _perm_parity(h) == _perm_parity(q)
+        # distinct residues per slot within each batch of 32
+        res = np.where(used[:, None], r[:, k:2 * k].astype(int) % 32, -1 - np.arange(size)[:, None])
+        for b in range(size // 32):
+            blk = res[32 * b:32 * b + 32]
+            for l in range(k):
+                assert len(set(blk[:, l].tolist())) == 32
 
 
 def test_device_layout_plan_edge_cases(lib):
