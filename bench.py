@@ -54,27 +54,55 @@ def load_peaks():
 # ----------------------------------------------------------------------------------------
 # work model of the excitation-sweep kernel (one launch = all walkers, one moved electron)
 # ----------------------------------------------------------------------------------------
-def sweep_work(problem, spin: int, W: int, mixed: bool):
-    """Algorithmic flops and HBM bytes of one excitation-sweep launch.
+def exc_flops(k: int) -> float:
+    """Flops of one excitation of order k in the sweep (FMA = 2): the pivoted elimination of
+    k - 2 columns, three FMA-corrected 2 x 2 determinants (6 flops each), the back
+    substitution of z = det T_u^{-1} x_u, and the accumulation C det into S_T and C z into G."""
+    if k <= 1:
+        return 4.0
+    f = 18.0
+    for j in range(k - 2):
+        r = k - 1 - j
+        f += r + 2.0 * r * r + 2.0 * r + 1.0   # multipliers, Schur update, right-hand side, 1/u_jj
+    f += (k - 2) + 1 + 2                       # product of pivots, det, scaling of z_2
+    for q in range(k - 2):
+        f += 2 + 2.0 * (k - 1 - q)             # back substitution of z_1
+    return f + 2.0 + 2.0 * k
 
-    Per walker: sum_k n_k ((2/3) k^3 + 2 k^2 + 10 k + 10) flops for the excitations (one
-    shared LU of T_u, one solve, five bordered channels, five CI multiply-adds), plus
-    10 n m for the five virtual-row contractions and 10 n for rho and s^a.  Bytes per
-    walker: the C stream (n_exc values), the table T (n m values), the column of A_0^{-1},
-    the five orbital rows at r', and the y row written for the accept step; the shared
-    excitation lists once per launch.
+
+def sweep_work(problem, spin: int, W: int, mixed: bool, n_exc_internal: int):
+    """Algorithmic flops and HBM bytes of one excitation-sweep launch (all W walkers).
+
+    Per walker: sum over strings of exc_flops(k) (dense singles: 4 per table entry), 2 n m for
+    T G, 2 n m for the kept y^0 row, 10 (n + m) for the five channel dot products and 10 n for
+    rho and s^a.  Bytes per walker: the C stream (one value per internal string, padding
+    included), the table T, the column of A_0^{-1}, the five orbital rows at r' and the y^0 row
+    written; the excitation records once per launch.
     """
     n, N = problem.n_elec[spin], problem.n_orb[spin]
     m = N - n
-    k = problem.exc_orders(spin)
-    hist = np.bincount(k, minlength=9)
-    f = sum(int(hist[q]) * ((2.0 / 3.0) * q ** 3 + 2 * q * q + 10 * q + 10) for q in range(1, 9))
-    f += 5 * int(hist[0]) * 2
-    f += 10.0 * n * m + 10.0 * n
+    hist = np.bincount(problem.exc_orders(spin), minlength=9)
+    dense = hist[1] > 0 and 4 * hist[1] >= n * m
+    f = 4.0 * n * m if dense else hist[1] * exc_flops(1)
+    f += sum(int(hist[q]) * exc_flops(q) for q in range(2, 9))
+    f += 4.0 * n * m + 10.0 * (n + m) + 10.0 * n
     b = 4 if mixed else 8
-    per_walker = problem.n_exc(spin) * b + n * m * b + n * 8 + 5 * N * b + m * b + 6 * 8
+    per_walker = n_exc_internal * b + n * m * b + n * 8 + 5 * N * b + m * b + 6 * 8
     lists = sum(int(hist[q]) * (2 if q <= 1 else 4 if q == 2 else 8 if q <= 4 else 16) for q in range(1, 9))
     return f * W, per_walker * W + lists
+
+
+def profiled_traffic(mixed: bool):
+    """DRAM bytes per walker of the sweep kernel from the committed ncu summary, or None."""
+    name = "k_ratio_large_mixed.md" if mixed else "k_ratio_large_fp64.md"
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("dram_bytes_per_walker:"):
+                return float(line.split(":")[1])
+    return None
 
 
 class ClockSampler:
@@ -172,12 +200,20 @@ def oracle_rate(wl, n_moves: int, time_cap: float):
     return done / dt, done, dt, orc.num_threads()
 
 
+def workload_desc(name, wl):
+    p = wl.problem
+    return (f"{name}: {p.n_elec[0]}+{p.n_elec[1]} electrons, {p.n_orb[0]} orbitals per spin, {p.n_basis} "
+            f"Gaussians, {p.n_det} determinants ({p.n_exc(0)}+{p.n_exc(1)} unique strings), {wl.n_walkers} walkers "
+            f"per GPU, refresh every {wl.refresh_K} steps of a spin")
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     from paper_1106_2456_gb300 import workloads
 
+    full = workloads.make_workload(args.workload, **({"n_walkers": args.walkers} if args.walkers else {}))
     wl = workloads.make_workload(args.workload, n_walkers=2)
     warm = min(args.warmup, 1)
     if warm:
@@ -188,7 +224,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws, "steps": done,
             "warmup": warm, "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "walkers_per_step": 1, "precision": "fp64 (oracle)"},
+            "config": {"workload": workload_desc(args.workload, full), "walkers_per_step": 1,
+                       "precision": "fp64 (oracle: every determinant by LU)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -215,7 +252,7 @@ def run_ours(args):
         dist.barrier()
     msd.load_library()
     peaks, peak_kind = load_peaks()
-    wl = workloads.make_workload(args.workload)
+    wl = workloads.make_workload(args.workload, **({"n_walkers": args.walkers} if args.walkers else {}))
     p = wl.problem
     W = wl.n_walkers
     K = wl.refresh_K
@@ -279,9 +316,10 @@ def run_ours(args):
     def roofline(prec, sweep_ms, steps):
         mixed = prec == "mixed"
         F = B = 0.0
+        plan = msd.describe(p, prec)
         for t in range(args.warmup, args.warmup + steps):
             s = p.spin_of(t % n_tot)
-            f, b = sweep_work(p, s, W, mixed)
+            f, b = sweep_work(p, s, W, mixed, int(plan[s][0]))
             F += f
             B += b
         sec = sweep_ms * 1e-3
@@ -296,7 +334,10 @@ def run_ours(args):
                else "nominal GB300 FP64 rate"}
         main = dict(alu if t_alu >= t_hbm else hbm)
         main["bound"] = "alu" if t_alu >= t_hbm else "hbm"
-        main["traffic"] = None
+        tb = profiled_traffic(mixed)
+        main["traffic"] = None if tb is None else tb * W
+        main["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per walker (1024-walker capture, "
+                                  "profiles/) x walkers" if tb is not None else None)
         main["kernel"] = "k_ratio (excitation sweep, steps A2-A5)"
         main["launches"] = steps
         main["avg_launch_us"] = 1e3 * sweep_ms / steps
@@ -310,10 +351,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {p.n_elec[0]}+{p.n_elec[1]} electrons, {p.n_orb[0]} orbitals "
-                                   f"per spin, {p.n_basis} Gaussians, {p.n_det} determinants "
-                                   f"({p.n_exc(0)}+{p.n_exc(1)} unique strings), {W} walkers per GPU, "
-                                   f"refresh every {K} steps of a spin",
+            "config": {"workload": workload_desc(args.workload, wl),
                        "precision": "mixed: FP32 orbitals/table/excitation dets, FP64 inverse/SM/ratio sums",
                        "walkers_per_gpu": W, "parallelism": f"replicas x{ws}",
                        "l2": "inputs exceed L2 (per-walker tables and CI streams: >1 GB)"},
@@ -403,11 +441,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=128)
     ap.add_argument("--cmp-steps", type=int, default=16)
-    ap.add_argument("--cpu-moves", type=int, default=6)
+    ap.add_argument("--cpu-moves", type=int, default=30)
     ap.add_argument("--cpu-time-cap", type=float, default=25.0)
     ap.add_argument("--ref-time-cap", type=float, default=150.0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--walkers", type=int, default=0, help="override the workload's walker count (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

@@ -233,9 +233,11 @@ msd_status validate(const msd_problem* p) {
 // string goes to the first of the kWindow most recently opened batches where a slot assignment
 // exists (a bipartite matching of its particles to free slots), else opens a new batch; unused
 // slots hold kEmptyRecord records.
+// Without `conflict_free` (FP64 tables, whose sweep is bound by FP64 arithmetic rather than by
+// shared-memory banks) the strings fill the batches in their sorted order.
 // Returns the number of internal slots used (a multiple of kBatch).
 int pack_group(SpinConst& S, const msd_problem* p, int s, int k, const int* members, int count, int idx0,
-               std::vector<uint8_t>& rec) {
+               std::vector<uint8_t>& rec, bool conflict_free) {
     constexpr int kWindow = 512;
     const int32_t* off = p->exc_off[s];
     struct Batch {
@@ -273,8 +275,13 @@ int pack_group(SpinConst& S, const msd_problem* p, int s, int k, const int* memb
         for (int i = 0; i < k; ++i) res[i] = p->exc_parts[s][off[u] + i] & 31;
         int bi = -1;
         const int last = (int)batches.size();
-        for (int b = std::max(first_open, last - kWindow); b < last && bi < 0; ++b)
-            if (batches[b].cnt < kBatch && fits(batches[b])) bi = b;
+        if (!conflict_free) {
+            if (last > 0 && batches[last - 1].cnt < kBatch) bi = last - 1;
+            for (int i = 0; i < k; ++i) slot[i] = i;
+        } else {
+            for (int b = std::max(first_open, last - kWindow); b < last && bi < 0; ++b)
+                if (batches[b].cnt < kBatch && fits(batches[b])) bi = b;
+        }
         if (bi < 0) {
             batches.push_back(Batch{});
             bi = (int)batches.size() - 1;
@@ -355,7 +362,7 @@ msd_status plan_strings(SpinConst& S, const msd_problem* p, int s) {
             }
             idx += S.n * S.m;
         } else if (pos > first) {
-            idx += pack_group(S, p, s, k, order.data() + first, pos - first, idx, rec);
+            idx += pack_group(S, p, s, k, order.data() + first, pos - first, idx, rec, p->prec == MSD_MIXED);
         }
     }
     while (rec.size() % 16) rec.push_back(0);

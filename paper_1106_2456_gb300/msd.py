@@ -122,6 +122,54 @@ def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, shape=None, name: str =
     return t.data_ptr()
 
 
+def problem_struct(problem, n_walkers: int, precision: str, refresh_K: int = 1 << 30, stream_handle=None):
+    """The msd_problem struct of a workloads.Problem, and the arrays it points into (keep them alive)."""
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dtype=dt)
+        if a.size == 0:
+            a = np.zeros(1, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    s = _Problem()
+    s.n_elec[0], s.n_elec[1] = problem.n_elec
+    s.n_orb[0], s.n_orb[1] = problem.n_orb
+    s.n_nuc = problem.nuc_xyz.shape[0]
+    s.nuc_xyz = arr(problem.nuc_xyz, np.float64)
+    s.n_basis = problem.n_basis
+    s.bas_center = arr(problem.bas_center, np.int32)
+    s.bas_lm = arr(problem.bas_lm, np.int8)
+    s.bas_alpha = arr(problem.bas_alpha, np.float64)
+    for k in range(2):
+        s.B[k] = arr(problem.B[k], np.float64)
+        s.n_exc[k] = problem.n_exc(k)
+        s.exc_off[k] = arr(problem.exc_off[k], np.int32)
+        s.exc_holes[k] = arr(problem.exc_holes[k], np.uint8)
+        s.exc_parts[k] = arr(problem.exc_parts[k], np.uint8)
+    s.n_det = problem.n_det
+    s.det_up = arr(problem.det_up, np.int32)
+    s.det_dn = arr(problem.det_dn, np.int32)
+    s.ci = arr(problem.ci, np.float64)
+    s.n_walkers = int(n_walkers)
+    s.prec = MSD_MIXED if precision == "mixed" else MSD_FP64
+    s.refresh_K = int(min(refresh_K, 2 ** 31 - 1))
+    s.cuda_stream = stream_handle
+    return s, keep
+
+
+def describe(problem, precision: str = "mixed") -> np.ndarray:
+    """msd_describe: the device layout msd_init builds, [2 spins][16] (no GPU needed)."""
+    lib = load_library()
+    s, keep = problem_struct(problem, 1, precision)
+    out = np.zeros(32, dtype=np.int64)
+    rc = lib.msd_describe(ctypes.byref(s), out.ctypes.data)
+    if rc != 0:
+        raise MSDError(rc, lib.msd_last_error(None).decode())
+    return out.reshape(2, 16)
+
+
 class MSD:
     """One libmsd context: a multi-determinant wavefunction and W walkers on the current GPU."""
 
@@ -137,38 +185,7 @@ class MSD:
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        keep = []
-
-        def arr(x, dt):
-            a = np.ascontiguousarray(x, dtype=dt)
-            if a.size == 0:
-                a = np.zeros(1, dtype=dt)
-            keep.append(a)
-            return a.ctypes.data
-
-        s = _Problem()
-        s.n_elec[0], s.n_elec[1] = problem.n_elec
-        s.n_orb[0], s.n_orb[1] = problem.n_orb
-        s.n_nuc = problem.nuc_xyz.shape[0]
-        s.nuc_xyz = arr(problem.nuc_xyz, np.float64)
-        s.n_basis = problem.n_basis
-        s.bas_center = arr(problem.bas_center, np.int32)
-        s.bas_lm = arr(problem.bas_lm, np.int8)
-        s.bas_alpha = arr(problem.bas_alpha, np.float64)
-        for k in range(2):
-            s.B[k] = arr(problem.B[k], np.float64)
-            s.n_exc[k] = problem.n_exc(k)
-            s.exc_off[k] = arr(problem.exc_off[k], np.int32)
-            s.exc_holes[k] = arr(problem.exc_holes[k], np.uint8)
-            s.exc_parts[k] = arr(problem.exc_parts[k], np.uint8)
-        s.n_det = problem.n_det
-        s.det_up = arr(problem.det_up, np.int32)
-        s.det_dn = arr(problem.det_dn, np.int32)
-        s.ci = arr(problem.ci, np.float64)
-        s.n_walkers = self.W
-        s.prec = MSD_MIXED if self.mixed else MSD_FP64
-        s.refresh_K = int(min(refresh_K, 2 ** 31 - 1))
-        s.cuda_stream = self.stream.cuda_stream
+        s, self._keep = problem_struct(problem, self.W, precision, refresh_K, self.stream.cuda_stream)
         ctx = ctypes.c_void_p()
         rc = self.lib.msd_init(ctypes.byref(s), 1, ctypes.byref(ctx))
         if rc != 0:

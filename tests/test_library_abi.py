@@ -24,7 +24,7 @@ def test_exports_every_declared_function(lib):
     assert missing == []
 
 
-def _struct(problem, W=4, prec=0, K=5):
+def _struct(problem, W=4, prec=1, K=5):
     keep = []
 
     def arr(x, dt):
@@ -181,8 +181,25 @@ def test_device_layout_plan(lib, label, kw):
         _check_records(lib, p, s, goff, dense)
 
 
-def _records(lib, problem, spin):
-    s, keep = _struct(problem)
+def test_device_layout_plan_fp64():
+    """FP64 tables: batches filled in sorted order, padding only at the end of each order."""
+    lib = msd.load_library()
+    p = wl.make_workload("medium", n_walkers=2).problem
+    s, keep = _struct(p, prec=0)
+    out = np.zeros(32, dtype=np.int64)
+    assert lib.msd_describe(ctypes.byref(s), out.ctypes.data) == 0
+    d = out.reshape(2, 16)
+    for sp in range(2):
+        hist = np.bincount(p.exc_orders(sp), minlength=9)
+        sizes = np.diff(d[sp, 5:15])
+        dense = bool(d[sp, 1])
+        for k in range(2 if dense else 1, 9):
+            assert sizes[k] == -(-hist[k] // 32) * 32
+        _check_records(lib, p, sp, d[sp, 5:15], dense, conflict_free=False)
+
+
+def _records(lib, problem, spin, prec=1):
+    s, keep = _struct(problem, prec=prec)
     off = np.zeros(10, dtype=np.int64)
     nbytes = ctypes.c_int64()
     assert lib.msd_describe_records(ctypes.byref(s), spin, None, 0, off.ctypes.data, ctypes.byref(nbytes)) == 0
@@ -198,10 +215,10 @@ def _perm_parity(a):
     return inv & 1
 
 
-def _check_records(lib, p, spin, goff, dense):
+def _check_records(lib, p, spin, goff, dense, conflict_free=True):
     """Every string of order k appears once in its group's records, holes and particles
     permuted with equal parity; slots of a batch hold distinct particle residues mod 32."""
-    out, off = _records(lib, p, spin)
+    out, off = _records(lib, p, spin, prec=1 if conflict_free else 0)
     rb = {1: 2, 2: 4, 3: 8, 4: 8}
     offs = p.exc_off[spin]
     for k in range(2 if dense else 1, 9):
@@ -218,6 +235,8 @@ def _check_records(lib, p, spin, goff, dense):
         assert got == want
         for h, q in zip(holes, parts):
             assert _perm_parity(h) == _perm_parity(q)
+        if not conflict_free:
+            continue
         # distinct residues per slot within each batch of 32
         res = np.where(used[:, None], r[:, k:2 * k].astype(int) % 32, -1 - np.arange(size)[:, None])
         for b in range(size // 32):
