@@ -204,6 +204,21 @@ msd_status msd_exc_histogram(const msd_ctx* ctx, int32_t spin, int64_t* out);
 msd_status msd_timing_start(msd_ctx* ctx);
 msd_status msd_timing_stop(msd_ctx* ctx, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches);
 
+/* msd_ratio without any device allocation and without keeping a proposal (the paper has no
+ * counterpart: it is a library concern).  Same arguments and results as msd_ratio for the
+ * current state, but the orbitals at rnew_dev go to a fixed device array of 4 MiB inside the
+ * library instead of the context's proposal buffers, so a pending msd_ratio proposal stays
+ * valid for msd_accept and the refresh counter does not advance.  Meant for callers that may
+ * not allocate device memory when they need extra ratios (allocation can synchronise the
+ * device, or the device memory is already reserved by another allocator).
+ * Limits and rules: W x (5 with grad/lap, else 1) x N_spin x (8 FP64, 4 mixed) bytes must fit
+ * in 4 MiB, else MSD_ERR_ARG; the array is shared by every context on a device, so calls that
+ * overlap in time on one device race and must be serialised by the caller; the first call on
+ * each device looks the array's address up (with that device current) and must come before
+ * any stream capture the caller starts.  Nothing is allocated or freed by this call. */
+msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev,
+                             double* grad_dev, double* lap_dev);
+
 /* Release every device and host resource of the context (NULL is a no-op). */
 void msd_destroy(msd_ctx* ctx);
 

@@ -870,4 +870,36 @@ void msd_destroy(msd_ctx* c) {
     delete c;
 }
 
+msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
+                             double* lap_dev) {
+    if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if ((grad_dev == nullptr) != (lap_dev == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    State& st = c->st;
+    const int s = spin_of(c, elec);
+    const SpinConst& S = c->sp[s];
+    const int nch = grad_dev ? NCH : 1;
+    const size_t need = (size_t)c->W * nch * S.N * c->tb;
+    if (need > kNoAllocScratchBytes)
+        return fail(c, MSD_ERR_ARG,
+                    "msd_ratio_noalloc needs %zu bytes of scratch (walkers x channels x orbitals x %d bytes), "
+                    "above its fixed limit of %zu bytes; use msd_ratio",
+                    need, c->tb, kNoAllocScratchBytes);
+    void* phi = nullptr;
+    cudaError_t e = noalloc_scratch(&phi);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
+    TRY(ensure_C(c, st, s));
+    launch_orbitals(c->L(), c->mixed, nch, c->W, 1, rnew_dev, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, phi);
+    RatioArgs a{};
+    a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = elec - S.off; a.nch = nch;
+    a.phi = phi; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
+    a.ratio = ratio_dev; a.rs = 1; a.grad = grad_dev; a.gs = 3; a.lap = lap_dev; a.ls = 1;
+    a.rho = nullptr; a.num = nullptr; a.y0 = nullptr;
+    if (S.m == 0) a.g.kmax = 0;
+    launch_ratio(c->L(), c->mixed, a);
+    return check_launch(c, "ratio (no allocation)");
+}
+
 }  // extern "C"

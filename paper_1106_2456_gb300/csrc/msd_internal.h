@@ -126,4 +126,9 @@ void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, 
 
 size_t ratio_smem_bytes(bool mixed, int n, int m, int nch);
 
+// Fixed device scratch of msd_ratio_noalloc (msd_kernels.cu): its size, and its address on the
+// current device (looked up on the first call per device).
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
+cudaError_t noalloc_scratch(void** ptr);
+
 }  // namespace msd

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "msd_internal.h"
@@ -998,6 +999,41 @@ void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, 
                   const double* S, double* logabs, double* sign) {
     L.count();
     k_state<<<(W + 255) / 256, 256, 0, L.stream>>>(W, ld0, sg0, ld1, sg1, S, logabs, sign);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fixed device scratch for msd_ratio_noalloc
+// ------------------------------------------------------------------------------------------
+// Some callers may not allocate device memory at the moment they need a ratio: cudaMalloc and
+// cudaFree can synchronise the whole device (stalling every other stream of the process), and a
+// process whose device memory is already reserved by another framework's caching allocator
+// may have nothing left to give.  For them msd_ratio_noalloc keeps the orbitals at the trial
+// positions in this file-scope array instead of a buffer of the context.  One array exists per
+// device and every call on that device uses all of it, so two calls that overlap in time on one
+// device (two streams, two host threads, two contexts) race on it; callers serialise them.
+// Nothing in it needs to start at zero: the orbital kernel writes every entry the sweep reads.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static constexpr int kNoAllocMaxDevices = 64;
+
+cudaError_t noalloc_scratch(void** ptr) {
+    // Address looked up once per device, with that device current, on its first use (a runtime
+    // query, not an allocation); a caller's first call on a device must therefore come before
+    // any stream capture it starts.
+    static std::mutex mu;
+    static void* addr[kNoAllocMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace msd

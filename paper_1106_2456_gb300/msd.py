@@ -84,6 +84,7 @@ def load_library():
         "msd_set_positions": ([vp, vp], i32),
         "msd_ratio": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_accept": ([vp, i32, vp], i32),
+        "msd_ratio_noalloc": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_grad_lap": ([vp, i32, vp, vp], i32),
         "msd_eval_batch": ([vp, vp, vp, vp, vp, vp], i32),
         "msd_get_state": ([vp, vp, vp, vp], i32),
@@ -223,6 +224,16 @@ class MSD:
                                        _dptr(ratio, torch.float64, (W,), "ratio"),
                                        _dptr(grad, torch.float64, (W, 3), "grad"),
                                        _dptr(lap, torch.float64, (W,), "lap")))
+
+    def ratio_noalloc_into(self, elec: int, rnew: torch.Tensor, ratio: torch.Tensor,
+                           grad: Optional[torch.Tensor] = None, lap: Optional[torch.Tensor] = None):
+        """msd_ratio_noalloc: ratio (and grad/lap) at rnew with no device allocation and no
+        proposal kept; a pending msd_ratio proposal stays valid."""
+        W = self.W
+        self._check(self.lib.msd_ratio_noalloc(self.ctx, int(elec), _dptr(rnew, torch.float64, (W, 3), "rnew"),
+                                               _dptr(ratio, torch.float64, (W,), "ratio"),
+                                               _dptr(grad, torch.float64, (W, 3), "grad"),
+                                               _dptr(lap, torch.float64, (W,), "lap")))
 
     def ratio(self, elec: int, rnew: torch.Tensor, with_grad: bool = True):
         r = self._empty(self.W)

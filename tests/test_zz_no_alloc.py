@@ -1,0 +1,87 @@
+"""msd_ratio_noalloc (orbitals at the trial positions in a fixed device array, no allocation)
+against msd_ratio on the same state, two calls in a row; a pending msd_ratio proposal must
+survive it, and a request above the fixed scratch size must be refused."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1106_2456_gb300 import msd, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _close(a, b, prec):
+    # FP64 G copies are shared by warp pairs (atomics), so launches may differ in the last bits;
+    # the mixed path runs the same kernels on the same inputs
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    return bool(((a - b).abs() <= tol * b.abs().clamp_min(1.0)).all())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_matches_ratio_twice(prec):
+    w = wl.make_workload("water", n_walkers=48)
+    p = w.problem
+    ctx = msd.MSD(p, w.n_walkers, prec, refresh_K=w.refresh_K)
+    ctx.set_positions(torch.tensor(w.R0, device="cuda"))
+    eta, _ = w.proposals(3)
+    for t, e in enumerate((2, 7, 0)):
+        rnew = torch.tensor(w.R0[:, e] + w.tau * eta[t], device="cuda")
+        r0, g0, l0 = ctx.ratio(e, rnew)
+        for _ in range(2):
+            r1, g1, l1 = torch.empty_like(r0), torch.empty_like(g0), torch.empty_like(l0)
+            ctx.ratio_noalloc_into(e, rnew, r1, g1, l1)
+            assert _close(r1, r0, prec) and _close(g1, g0, prec) and _close(l1, l0, prec)
+        r2 = torch.empty_like(r0)
+        ctx.ratio_noalloc_into(e, rnew, r2)
+        assert _close(r2, r0, prec)
+    ctx.sync()
+    ctx.close()
+
+
+def test_pending_proposal_survives():
+    w = wl.make_workload("water", n_walkers=32)
+    p = w.problem
+    a = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    b = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    R = torch.tensor(w.R0, device="cuda")
+    a.set_positions(R)
+    b.set_positions(R)
+    eta, u = w.proposals(2)
+    e = 3
+    rnew = torch.tensor(w.R0[:, e] + w.tau * eta[0], device="cuda")
+    other = torch.tensor(w.R0[:, e] + w.tau * eta[1], device="cuda")
+    ra, _, _ = a.ratio(e, rnew)
+    rb, _, _ = b.ratio(e, rnew)
+    scratch = torch.empty_like(ra)
+    a.ratio_noalloc_into(e, other, scratch, torch.empty(w.n_walkers, 3, dtype=torch.float64, device="cuda"),
+                         torch.empty_like(ra))
+    acc = torch.tensor((u[0] < (ra * ra).cpu().numpy()).astype(np.uint8), device="cuda")
+    a.accept(e, acc)
+    b.accept(e, acc)
+    Ra, la, sa = a.get_state()
+    Rb, lb, sb = b.get_state()
+    assert torch.equal(Ra, Rb) and torch.equal(sa, sb)
+    assert torch.allclose(la, lb, rtol=0, atol=1e-12)
+    a.close()
+    b.close()
+
+
+def test_oversize_is_refused():
+    w = wl.make_workload("medium", n_walkers=1024)  # 1024 x 5 x 120 x 8 bytes > 4 MiB
+    ctx = msd.MSD(w.problem, w.n_walkers, "fp64")
+    ctx.set_positions(torch.tensor(w.R0, device="cuda"))
+    rnew = torch.tensor(w.R0[:, 0], device="cuda")
+    out = torch.empty(w.n_walkers, dtype=torch.float64, device="cuda")
+    with pytest.raises(msd.MSDError, match="MSD_ERR_ARG.*fixed limit"):
+        ctx.ratio_noalloc_into(0, rnew, out, torch.empty(w.n_walkers, 3, dtype=torch.float64, device="cuda"),
+                               torch.empty_like(out))
+    ctx.ratio_noalloc_into(0, rnew, out)  # one channel fits: 1024 x 120 x 8 bytes
+    ctx.sync()
+    ctx.close()
