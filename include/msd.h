@@ -204,6 +204,20 @@ msd_status msd_exc_histogram(const msd_ctx* ctx, int32_t spin, int64_t* out);
 msd_status msd_timing_start(msd_ctx* ctx);
 msd_status msd_timing_stop(msd_ctx* ctx, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches);
 
+/* Adjoint of log|Psi| at the current positions, summed over walkers with weights gbar_dev [W]:
+ * dci_dev [n_det] = sum_w gbar[w] d log|Psi_w| / d c_I and dB_dev = sum_w gbar[w]
+ * d log|Psi_w| / d B_s for each spin, laid out as B_up [n_basis][n_orb[0]] followed by
+ * B_dn [n_basis][n_orb[1]] (a restricted B that the caller shares between spins gets the sum
+ * of the two blocks).  Both outputs are overwritten.  The paper gives no parameter
+ * derivatives; they follow from Psi = sum_I c_I det A_up,I det A_dn,I (Section II) with the
+ * excitation ratios t_u = det T_u of Section III: d/dc_I = t_up t_dn / S; d/dT = (1/S)
+ * sum_u C_u cof(T_u); d/dPhi = A_0^{-T}[I - Tbar T^T | Tbar]; d/dB = chi^T Phibar.
+ * Recomputes A_0^{-1}, T, the excitation values and S from scratch first (any pending
+ * msd_ratio proposal is dropped).  The first call allocates its workspace (W x n x N and
+ * W x n x n_basis doubles).  MSD_ERR_ARG if a spin's table and its adjoint do not fit in
+ * one SM's shared memory. */
+msd_status msd_backward(msd_ctx* ctx, const double* gbar_dev, double* dci_dev, double* dB_dev);
+
 /* msd_ratio without any device allocation and without keeping a proposal (the paper has no
  * counterpart: it is a library concern).  Same arguments and results as msd_ratio for the
  * current state, but the orbitals at rnew_dev go to a fixed device array of 4 MiB inside the

@@ -80,6 +80,12 @@ struct msd_ctx {
     // staging for the host-buffer entry points
     double* d_io = nullptr;    // [W][8]
     uint8_t* d_acc = nullptr;  // [W]
+    // msd_backward: internal strings of every term, and workspace allocated on first use
+    long long n_det = 0;
+    int* term_iu = nullptr;    // [n_det] internal up string of term I
+    int* term_id = nullptr;    // [n_det] internal down string of term I
+    double* bw_M = nullptr;    // [W][n_max][N_max]
+    double* bw_chi = nullptr;  // [W n_max][n_basis]
     std::vector<void*> allocs;
     std::string err;
     // measurement: kernel launch count and events around the excitation-sweep kernel
@@ -584,6 +590,16 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     if ((st = dalloc(c, &c->d_status, 1)) != MSD_OK) return bail(st);
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(c, MSD_ERR_CUDA, "memset"));
     if ((st = alloc_state(c, c->st)) != MSD_OK) return bail(st);
+    {
+        c->n_det = p->n_det;
+        std::vector<int> iu(p->n_det), id(p->n_det);
+        for (int64_t I = 0; I < p->n_det; ++I) {
+            iu[I] = c->sp[0].internal_of[p->det_up[I]];
+            id[I] = c->sp[1].internal_of[p->det_dn[I]];
+        }
+        if ((st = upload(c, &c->term_iu, iu.data(), iu.size())) != MSD_OK) return bail(st);
+        if ((st = upload(c, &c->term_id, id.data(), id.size())) != MSD_OK) return bail(st);
+    }
     *out = c;
     return MSD_OK;
 }
@@ -900,6 +916,47 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
     if (S.m == 0) a.g.kmax = 0;
     launch_ratio(c->L(), c->mixed, a);
     return check_launch(c, "ratio (no allocation)");
+}
+
+msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, double* dB_dev) {
+    if (!c || !gbar_dev || !dci_dev || !dB_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    for (int s = 0; s < 2; ++s) {
+        const SpinConst& S = c->sp[s];
+        if (tbar_smem_bytes(c->mixed, S.n, S.m) > 220 * 1024)
+            return fail(c, MSD_ERR_ARG, "spin %d: table and its adjoint (%d x %d) do not fit in shared memory", s, S.n,
+                        S.m);
+    }
+    State& st = c->st;
+    const size_t W = c->W;
+    const int nmax = std::max(c->sp[0].n, c->sp[1].n);
+    const int Nmax = std::max(c->sp[0].N, c->sp[1].N);
+    if (!c->bw_M) TRY(dalloc(c, &c->bw_M, W * nmax * Nmax));
+    if (!c->bw_chi) TRY(dalloc(c, &c->bw_chi, W * nmax * c->nb));
+    // every quantity from scratch at the current positions (as msd_set_positions does)
+    c->prop_valid = false;
+    TRY(refresh_spin(c, st, 0));
+    TRY(refresh_spin(c, st, 1));
+    st.C_valid[0] = st.C_valid[1] = false;
+    TRY(ensure_C(c, st, 0));     // t_dn, C_up
+    TRY(recompute_S(c, st, 0));  // t_up, S
+    TRY(ensure_C(c, st, 1));     // C_dn
+    cudaError_t e = cudaMemsetAsync(dci_dev, 0, sizeof(double) * c->n_det, c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+    launch_dci(c->L(), c->mixed, c->W, c->n_det, c->term_iu, c->term_id, gbar_dev, st.S, st.t[0], c->sp[0].g.n_exc,
+               st.t[1], c->sp[1].g.n_exc, dci_dev);
+    double* dB = dB_dev;
+    for (int s = 0; s < 2; ++s) {
+        const SpinConst& S = c->sp[s];
+        launch_phibar(c->L(), c->mixed, c->W, S.n, S.m, S.N, S.g, st.T[s], st.C[s], st.S, st.Ainv[s], gbar_dev,
+                      c->bw_M);
+        launch_chi(c->L(), c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas, c->blm, c->nb, c->bw_chi);
+        e = cudaMemsetAsync(dB, 0, sizeof(double) * c->nb * S.N, c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+        launch_dB(c->L(), c->W * S.n, c->nb, S.N, c->bw_chi, c->bw_M, dB);
+        dB += (size_t)c->nb * S.N;
+    }
+    return check_launch(c, "backward");
 }
 
 }  // extern "C"

@@ -1,0 +1,277 @@
+// msd_backward.cu -- adjoint of log|Psi| with respect to the CI coefficients c_I and the
+// orbital coefficients B of each spin, accumulated over walkers with weights gbar[w]
+// (the gradient a parameter optimisation needs; the paper is silent on it).
+//
+// Per walker, with S = Psi / (det A_up,0 det A_dn,0) = sum_I c_I t_up[u_I] t_dn[d_I]:
+//   d log|Psi| / d c_I   = t_up[u_I] t_dn[d_I] / S
+//   d log|Psi| / d T[h][p] = Tbar[h][p] = (1/S) sum_u C_u cof(T_u)[q][l]   (h = h_q, p = p_l)
+//   d log|Psi| / d Phi  = Ainv^T [ I - Tbar T^T | Tbar ]    (log|det A_0| and T = A_0^{-1} Phi_virt)
+//   d log|Psi| / d B[mu][j] = sum_r chi_mu(r_r) Phibar[r][j]
+// where cof(T_u) is the cofactor matrix of the k x k excitation block (Section III: t_u =
+// det T_u) and C_u the spin's CI weight of string u.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "msd_internal.h"
+#include "msd_records.cuh"
+#include "msd_smalldet.cuh"
+
+namespace msd {
+namespace {
+
+constexpr int kBB = 256;
+
+// ------------------------------------------------------------------------------------------
+// d log|Psi| / d c_I, summed over walkers: one thread per term, a slice of walkers per block row
+// ------------------------------------------------------------------------------------------
+template <typename TT>
+__global__ void __launch_bounds__(kBB) k_dci(int W, int wchunk, long long n_det, const int* __restrict__ iu,
+                                            const int* __restrict__ id, const double* __restrict__ gbar,
+                                            const double* __restrict__ S, const TT* __restrict__ t0, int ld0,
+                                            const TT* __restrict__ t1, int ld1, double* __restrict__ dci) {
+    const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= n_det) return;
+    const int a = iu[I], b = id[I];
+    const int w0 = blockIdx.y * wchunk, w1 = min(W, w0 + wchunk);
+    double acc = 0.0;
+    for (int w = w0; w < w1; ++w)
+        acc = fma(gbar[w] / S[w], double(t0[(long long)w * ld0 + a]) * double(t1[(long long)w * ld1 + b]), acc);
+    atomicAdd(dci + I, acc);
+}
+
+// ------------------------------------------------------------------------------------------
+// Tbar: scatter of cofactors of every excitation block, one block per walker
+// ------------------------------------------------------------------------------------------
+// cof(T_u)[q][l] = (-1)^(q+l) det(T_u without row q and column l), each minor by the same
+// pivoted small-determinant code the sweep uses.
+template <int K, typename TT>
+__device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], double cu,
+                                                  double* Tb) {
+    if constexpr (K == 1) {
+        atomicAdd(Tb + h[0] * m + p[0], cu);
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            int hh[K - 1];
+#pragma unroll
+            for (int i = 0; i < K - 1; ++i) hh[i] = h[i < q ? i : i + 1];
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                int pp[K - 1];
+#pragma unroll
+                for (int i = 0; i < K - 1; ++i) pp[i] = p[i < l ? i : i + 1];
+                const double minor = double(small_det<K - 1, TT>(Ts, m, hh, pp));
+                atomicAdd(Tb + h[q] * m + p[l], ((q + l) & 1) ? -cu * minor : cu * minor);
+            }
+        }
+    }
+}
+
+template <int K, typename TT>
+__device__ __forceinline__ void tbar_group(const ExcDev& g, const TT* Ts, int m, const TT* __restrict__ Cw,
+                                           double* Tb) {
+    const int j0 = g.goff[K], j1 = g.goff[K + 1];
+    const uint8_t* rec = g.rec + g.roff[K];
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        int h[K], p[K];
+        load_rec<K>(rec, j - j0, h, p);
+        const double cu = double(Cw[j]);
+        if (h[0] == kEmptyRecord || cu == 0.0) continue;
+        scatter_cofactors<K, TT>(Ts, m, h, p, cu, Tb);
+    }
+}
+
+// Writes Tbar / S into columns n..N-1 of M[w] (n x N, row stride N).
+template <typename TT>
+__global__ void __launch_bounds__(kBB) k_tbar(int n, int m, int N, ExcDev g, const TT* __restrict__ T,
+                                             const TT* __restrict__ C, const double* __restrict__ S,
+                                             double* __restrict__ M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* Tb = reinterpret_cast<double*>(smem);                                  // [n][m]
+    TT* Ts = reinterpret_cast<TT*>(smem + (((size_t)n * m * 8 + 15) & ~size_t(15)));  // [n][m]
+    const int w = blockIdx.x;
+    const TT* Tw = T + (long long)w * n * m;
+    const TT* Cw = C + (long long)w * g.n_exc;
+    for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
+        Ts[q] = Tw[q];
+        Tb[q] = g.dense1 ? double(Cw[g.goff[1] + q]) : 0.0;  // dense singles: d det T_u / d T[h][p] = 1
+    }
+    __syncthreads();
+    for (int k = g.dense1 ? 2 : 1; k <= g.kmax; ++k) {
+        switch (k) {
+            case 1: tbar_group<1, TT>(g, Ts, m, Cw, Tb); break;
+            case 2: tbar_group<2, TT>(g, Ts, m, Cw, Tb); break;
+            case 3: tbar_group<3, TT>(g, Ts, m, Cw, Tb); break;
+            case 4: tbar_group<4, TT>(g, Ts, m, Cw, Tb); break;
+            case 5: tbar_group<5, TT>(g, Ts, m, Cw, Tb); break;
+            case 6: tbar_group<6, TT>(g, Ts, m, Cw, Tb); break;
+            case 7: tbar_group<7, TT>(g, Ts, m, Cw, Tb); break;
+            case 8: tbar_group<8, TT>(g, Ts, m, Cw, Tb); break;
+        }
+    }
+    __syncthreads();
+    const double inv = 1.0 / S[w];
+    double* Mw = M + (long long)w * n * N;
+    for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
+        const int c = q / m, a = q - c * m;
+        Mw[(long long)c * N + n + a] = Tb[q] * inv;
+    }
+}
+
+// M[w][:, 0:n] = I - Tbar T^T  (Tbar read from M[w][:, n:N]); one block per walker.
+template <typename TT>
+__global__ void __launch_bounds__(kBB) k_tbar_tt(int n, int m, int N, const TT* __restrict__ T, double* __restrict__ M) {
+    const int w = blockIdx.x;
+    const TT* Tw = T + (long long)w * n * m;
+    double* Mw = M + (long long)w * n * N;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c1 = idx / n, c = idx - c1 * n;
+        const double* tb = Mw + (long long)c1 * N + n;
+        const TT* tr = Tw + (long long)c * m;
+        double acc = 0.0;
+        for (int a = 0; a < m; ++a) acc = fma(tb[a], double(tr[a]), acc);
+        Mw[(long long)c1 * N + c] = (c1 == c ? 1.0 : 0.0) - acc;
+    }
+}
+
+// M[w] <- gbar[w] Ainv[w]^T M[w] in place, one block per (walker, 32-column tile).
+__global__ void __launch_bounds__(kBB) k_phibar(int n, int N, const double* __restrict__ Ainv,
+                                               const double* __restrict__ gbar, double* __restrict__ M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* A = reinterpret_cast<double*>(smem);  // [n][n], A[c][r]
+    double* Mt = A + (size_t)n * n;               // [n][32]
+    const int w = blockIdx.x, j0 = blockIdx.y * 32;
+    const int nj = min(32, N - j0);
+    const double* Aw = Ainv + (long long)w * n * n;
+    double* Mw = M + (long long)w * n * N;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) A[q] = Aw[q];
+    for (int q = threadIdx.x; q < n * 32; q += blockDim.x) {
+        const int c = q >> 5, j = q & 31;
+        Mt[q] = j < nj ? Mw[(long long)c * N + j0 + j] : 0.0;
+    }
+    __syncthreads();
+    const double gw = gbar[w];
+    for (int q = threadIdx.x; q < n * 32; q += blockDim.x) {
+        const int r = q >> 5, j = q & 31;
+        if (j >= nj) continue;
+        double acc = 0.0;
+        for (int c = 0; c < n; ++c) acc = fma(A[c * n + r], Mt[c * 32 + j], acc);
+        Mw[(long long)r * N + j0 + j] = gw * acc;
+    }
+}
+
+// chi[p][mu] = chi_mu(r_p) (values only, FP64) at the electrons of one spin.
+__global__ void __launch_bounds__(kBB) k_chi(int P, int ppw, const double* __restrict__ pos, long long wstride,
+                                            int p_off, const double4* __restrict__ bas,
+                                            const int8_t* __restrict__ blm, int nb, double* __restrict__ chi) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * nb) return;
+    const int p = int(idx / nb), mu = int(idx - (long long)p * nb);
+    const int w = p / ppw, r = p - w * ppw;
+    const double* rp = pos + (long long)w * wstride + (long long)(p_off + r) * 3;
+    const double4 b = bas[mu];
+    const double d[3] = {rp[0] - b.x, rp[1] - b.y, rp[2] - b.z};
+    const double g = exp(-b.w * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    const int lm = blm[mu];
+    chi[idx] = lm == 0 ? g : d[lm - 1] * g;
+}
+
+// dB[mu][j] += sum_p chi[p][mu] Phibar[p][j] over a slice of points; 32 x 32 output tile per
+// block, 32-point steps through shared memory, one FP64 atomic per output at the end.
+__global__ void __launch_bounds__(kBB) k_dB(int P, int nb, int N, int pchunk, const double* __restrict__ chi,
+                                           const double* __restrict__ Phib, double* __restrict__ dB) {
+    __shared__ double Xs[32][33];
+    __shared__ double Ys[32][33];
+    const int mu0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int pa = blockIdx.z * pchunk, pb = min(P, pa + pchunk);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int p0 = pa; p0 < pb; p0 += 32) {
+        for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+            const int pp = q >> 5, cc = q & 31;
+            const int p = p0 + pp;
+            Xs[pp][cc] = (p < pb && mu0 + cc < nb) ? chi[(long long)p * nb + mu0 + cc] : 0.0;
+            Ys[pp][cc] = (p < pb && j0 + cc < N) ? Phib[(long long)p * N + j0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pp = 0; pp < 32; ++pp) {
+            const double y = Ys[pp][tx];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(Xs[pp][ty + 8 * i], y, acc[i]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int mu = mu0 + ty + 8 * i, j = j0 + tx;
+        if (mu < nb && j < N) atomicAdd(dB + (long long)mu * N + j, acc[i]);
+    }
+}
+
+}  // namespace
+
+void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* iu, const int* id, const double* gbar,
+                const double* S, const void* t0, int ld0, const void* t1, int ld1, double* dci) {
+    const int wchunk = 64;
+    dim3 grid((unsigned)((n_det + kBB - 1) / kBB), (unsigned)((W + wchunk - 1) / wchunk));
+    L.count();
+    if (mixed)
+        k_dci<float><<<grid, kBB, 0, L.stream>>>(W, wchunk, n_det, iu, id, gbar, S, static_cast<const float*>(t0), ld0,
+                                                  static_cast<const float*>(t1), ld1, dci);
+    else
+        k_dci<double><<<grid, kBB, 0, L.stream>>>(W, wchunk, n_det, iu, id, gbar, S, static_cast<const double*>(t0),
+                                                   ld0, static_cast<const double*>(t1), ld1, dci);
+}
+
+size_t tbar_smem_bytes(bool mixed, int n, int m) {
+    return (((size_t)n * m * 8 + 15) & ~size_t(15)) + (size_t)n * m * (mixed ? 4 : 8);
+}
+
+void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T,
+                   const void* C, const double* S, const double* Ainv, const double* gbar, double* M) {
+    const size_t sm = tbar_smem_bytes(mixed, n, m);
+    if (m > 0) {
+        if (mixed) {
+            cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            L.count();
+            k_tbar<float><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T),
+                                                    static_cast<const float*>(C), S, M);
+            L.count();
+            k_tbar_tt<float><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const float*>(T), M);
+        } else {
+            cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            L.count();
+            k_tbar<double><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+                                                     static_cast<const double*>(C), S, M);
+            L.count();
+            k_tbar_tt<double><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const double*>(T), M);
+        }
+    } else {
+        // no virtual orbitals: Phibar = gbar Ainv^T, M = I
+        L.count();
+        k_tbar_tt<double><<<W, kBB, 0, L.stream>>>(n, 0, N, nullptr, M);
+    }
+    const size_t sp = ((size_t)n * n + (size_t)n * 32) * 8;
+    cudaFuncSetAttribute(k_phibar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
+    L.count();
+    k_phibar<<<dim3(W, (N + 31) / 32), kBB, sp, L.stream>>>(n, N, Ainv, gbar, M);
+}
+
+void launch_chi(const Launch& L, int P, int ppw, const double* pos, long long wstride, int p_off, const double4* bas,
+                const int8_t* blm, int nb, double* chi) {
+    const long long total = (long long)P * nb;
+    L.count();
+    k_chi<<<(unsigned)((total + kBB - 1) / kBB), kBB, 0, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, chi);
+}
+
+void launch_dB(const Launch& L, int P, int nb, int N, const double* chi, const double* Phib, double* dB) {
+    const int pchunk = 4096;
+    dim3 grid((nb + 31) / 32, (N + 31) / 32, (P + pchunk - 1) / pchunk);
+    L.count();
+    k_dB<<<grid, kBB, 0, L.stream>>>(P, nb, N, pchunk, chi, Phib, dB);
+}
+
+}  // namespace msd

@@ -126,6 +126,19 @@ void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, 
 
 size_t ratio_smem_bytes(bool mixed, int n, int m, int nch);
 
+// Adjoint of log|Psi| (msd_backward.cu).  dci[I] += sum_w gbar[w] t0[w][iu[I]] t1[w][id[I]] / S[w].
+void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* iu, const int* id, const double* gbar,
+                const double* S, const void* t0, int ld0, const void* t1, int ld1, double* dci);
+// M[w] (n x N, FP64) <- gbar[w] Ainv[w]^T [I - Tbar T^T | Tbar], Tbar = (1/S) sum_u C_u cof(T_u).
+size_t tbar_smem_bytes(bool mixed, int n, int m);
+void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T,
+                   const void* C, const double* S, const double* Ainv, const double* gbar, double* M);
+// chi[p][mu] (values, FP64) at P points laid out as for launch_orbitals.
+void launch_chi(const Launch& L, int P, int ppw, const double* pos, long long wstride, int p_off, const double4* bas,
+                const int8_t* blm, int nb, double* chi);
+// dB[mu][j] += sum_p chi[p][mu] Phib[p][j].
+void launch_dB(const Launch& L, int P, int nb, int N, const double* chi, const double* Phib, double* dB);
+
 // Fixed device scratch of msd_ratio_noalloc (msd_kernels.cu): its size, and its address on the
 // current device (looked up on the first call per device).
 constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;

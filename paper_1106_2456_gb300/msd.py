@@ -85,6 +85,7 @@ def load_library():
         "msd_ratio": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_accept": ([vp, i32, vp], i32),
         "msd_ratio_noalloc": ([vp, i32, vp, vp, vp, vp], i32),
+        "msd_backward": ([vp, vp, vp, vp], i32),
         "msd_grad_lap": ([vp, i32, vp, vp], i32),
         "msd_eval_batch": ([vp, vp, vp, vp, vp, vp], i32),
         "msd_get_state": ([vp, vp, vp, vp], i32),
@@ -234,6 +235,16 @@ class MSD:
                                                _dptr(ratio, torch.float64, (W,), "ratio"),
                                                _dptr(grad, torch.float64, (W, 3), "grad"),
                                                _dptr(lap, torch.float64, (W,), "lap")))
+
+    def backward(self, gbar: torch.Tensor):
+        """msd_backward: (dci [n_det], (dB_up [n_basis, n_orb_up], dB_dn [n_basis, n_orb_dn])) of
+        sum_w gbar[w] log|Psi_w| at the current positions."""
+        nb, N0, N1 = self.p.n_basis, self.p.n_orb[0], self.p.n_orb[1]
+        dci = self._empty(self.p.n_det)
+        dB = self._empty(nb * (N0 + N1))
+        self._check(self.lib.msd_backward(self.ctx, _dptr(gbar, torch.float64, (self.W,), "gbar"),
+                                          dci.data_ptr(), dB.data_ptr()))
+        return dci, (dB[:nb * N0].view(nb, N0), dB[nb * N0:].view(nb, N1))
 
     def ratio(self, elec: int, rnew: torch.Tensor, with_grad: bool = True):
         r = self._empty(self.W)
