@@ -451,6 +451,15 @@ __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int l
     }
 }
 
+// Orders 5..8 are rare and need many registers: called out of line so that their register
+// pressure (and spills at the 80-register cap of three CTAs per SM) stays out of the code of
+// the common orders.
+template <int K, typename TT, int NGW>
+__device__ __noinline__ void sweep_group_outlined(const ExcDev& g, const TT* Ts, int ld, const TT* xs,
+                                                  const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int base) {
+    sweep_group<K, TT, NGW>(g, Ts, ld, xs, Cw, Gw, sacc, base);
+}
+
 struct RatioSmem {
     size_t ts, xd, xs, ph, g1, gw, tg, red, total;
 };
@@ -591,10 +600,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
             case 2: sweep_group<2, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
             case 3: sweep_group<3, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
             case 4: sweep_group<4, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 5: sweep_group<5, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 6: sweep_group<6, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 7: sweep_group<7, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 8: sweep_group<8, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 5: sweep_group_outlined<5, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 6: sweep_group_outlined<6, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 7: sweep_group_outlined<7, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 8: sweep_group_outlined<8, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
         }
     }
     __syncthreads();

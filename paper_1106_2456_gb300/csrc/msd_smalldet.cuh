@@ -39,11 +39,15 @@ MSD_HD T tabs(T x) {
     return x < T(0) ? -x : x;
 }
 
-// 1 / x: correctly rounded reciprocal (FP32 on the device avoids the IEEE division sequence).
+// 1 / x.  FP64: IEEE division.  FP32 on the device: the hardware approximation (PTX
+// rcp.approx.f32, at most 1 ulp from the exact reciprocal), one instruction instead of a
+// correctly rounded sequence; an LU multiplier then carries one extra rounding of that size.
 MSD_HD double recip(double x) { return 1.0 / x; }
 MSD_HD float recip(float x) {
 #if defined(__CUDA_ARCH__)
-    return __frcp_rn(x);
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 #else
     return 1.0f / x;
 #endif
@@ -214,31 +218,18 @@ MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], con
     }
 }
 
-// Per-thread accumulators of CI sums: plain FP64, or FP32 with Kahan compensation.
+// Per-thread accumulators of CI sums in the table's precision.  A thread adds at most a few
+// hundred terms of one walker's sum (the strings are spread over 256 threads), so plain FP32
+// accumulation adds a relative error of order 1e-5 of the sum of magnitudes, well inside the
+// FP32 path's accuracy; partial sums are combined across warps in FP64.
 template <typename TT, int NV>
-struct Accum;
-template <int NV>
-struct Accum<double, NV> {
-    double s[NV];
+struct Accum {
+    TT s[NV];
     MSD_HD void zero() {
-        for (int a = 0; a < NV; ++a) s[a] = 0.0;
+        for (int a = 0; a < NV; ++a) s[a] = TT(0);
     }
-    MSD_HD void add(int a, double x) { s[a] += x; }
-    MSD_HD double get(int a) const { return s[a]; }
-};
-template <int NV>
-struct Accum<float, NV> {
-    float s[NV], c[NV];
-    MSD_HD void zero() {
-        for (int a = 0; a < NV; ++a) s[a] = c[a] = 0.0f;
-    }
-    MSD_HD void add(int a, float x) {
-        const float y = x - c[a];
-        const float t = s[a] + y;
-        c[a] = (t - s[a]) - y;
-        s[a] = t;
-    }
-    MSD_HD double get(int a) const { return double(s[a]) - double(c[a]); }
+    MSD_HD void add(int a, TT x) { s[a] += x; }
+    MSD_HD double get(int a) const { return double(s[a]); }
 };
 
 }  // namespace msd
