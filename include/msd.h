@@ -26,8 +26,9 @@
  *     Pointers named *_host are HOST pointers; those calls synchronise.
  *   - Arrays are C-contiguous (row-major) with the stated shapes; W = n_walkers.
  *     Walker positions are [W][n_up + n_dn][3] doubles in bohr, up electrons first.
- *   - No call allocates after msd_init, except msd_eval_batch on first use (it
- *     creates a second walker state so that the main one is left untouched).
+ *   - No call allocates after msd_init, except on first use msd_eval_batch (it creates a
+ *     second walker state so that the main one is left untouched) and msd_backward (its
+ *     workspace).
  *   - Device-side numerical faults (a zero or non-finite pivot, a non-finite ratio)
  *     set a status word that msd_sync reports; host-side argument errors return
  *     MSD_ERR_ARG and leave the context unchanged.  msd_last_error explains the
@@ -96,10 +97,18 @@ typedef struct {
 
 typedef struct msd_ctx msd_ctx;
 
-/* Create a context for n_systems problems (only n_systems == 1 is accepted by this
- * build; batched uneven systems return MSD_ERR_ARG).  Validates every array, groups the
- * excitation strings by order and packs each order into batches of 32 for the device
- * (msd_describe_records), and allocates all per-walker state.  *out is NULL on failure. */
+/* Create a context.  n_systems == 1: prob points to one problem; msd_init validates every
+ * array, groups the excitation strings by order and packs each order into batches of 32 for
+ * the device (msd_describe_records), and allocates all per-walker state.
+ * n_systems > 1 (batched uneven systems): prob points to n_systems problems, each with its own
+ * electrons, orbitals, strings, terms and walkers (the paper treats one system; running many
+ * at once is a throughput concern).  Every per-walker array of every call is then the
+ * concatenation over systems in order (walkers of system 0, then of system 1, ...; positions
+ * [W_s][n_tot_s][3] per system; msd_backward's dci and dB likewise), and `elec` means electron
+ * (elec mod n_tot_s) of system s.  Systems run on internal streams forked from and joined
+ * back into the stream of prob[0], so the caller's stream orders every call as usual.
+ * msd_copy_state, msd_exc_histogram and msd_ratio_noalloc take single-system contexts only.
+ * *out is NULL on failure; the message names the failing system. */
 msd_status msd_init(const msd_problem* prob, int32_t n_systems, msd_ctx** out);
 
 /* Validate a problem and report, without any CUDA call, the device layout msd_init would

@@ -86,6 +86,12 @@ struct msd_ctx {
     int* term_id = nullptr;    // [n_det] internal down string of term I
     double* bw_M = nullptr;    // [W][n_max][N_max]
     double* bw_chi = nullptr;  // [W n_max][n_basis]
+    // batched uneven systems: one single-system context per system, run on kBatchStreams
+    // internal streams forked from and joined back into `stream`
+    std::vector<msd_ctx*> sub;
+    std::vector<long long> w_off, r_off, det_off, b_off;  // per system: walkers, positions, terms, B entries
+    std::vector<cudaStream_t> bstreams;
+    std::vector<cudaEvent_t> bevents;                       // [0] fork, [1 + i] join of stream i
     std::vector<void*> allocs;
     std::string err;
     // measurement: kernel launch count and events around the excitation-sweep kernel
@@ -525,12 +531,107 @@ msd_status grad_lap_one(msd_ctx* c, State& st, int e, double* grad, long long gs
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+bool is_batch(const msd_ctx* c) { return c && !c->sub.empty(); }
+
+// Make every internal stream wait for the work queued so far on the caller's stream.
+msd_status batch_fork(msd_ctx* c) {
+    cudaError_t e = cudaEventRecord(c->bevents[0], c->stream);
+    for (size_t i = 0; e == cudaSuccess && i < c->bstreams.size(); ++i)
+        e = cudaStreamWaitEvent(c->bstreams[i], c->bevents[0], 0);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "fork: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+// Make the caller's stream wait for everything queued on the internal streams.
+msd_status batch_join(msd_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; e == cudaSuccess && i < c->bstreams.size(); ++i) {
+        e = cudaEventRecord(c->bevents[1 + i], c->bstreams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->bevents[1 + i], 0);
+    }
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "join: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+// Run f(system index, sub-context) for every system between a fork and a join; the first
+// failure is reported with the system's index.
+template <typename F>
+msd_status batch_each(msd_ctx* c, F&& f) {
+    TRY(batch_fork(c));
+    for (size_t s = 0; s < c->sub.size(); ++s) {
+        const msd_status st = f((int)s, c->sub[s]);
+        if (st != MSD_OK) {
+            batch_join(c);
+            return fail(c, st, "system %zu: %s", s, c->sub[s]->err.c_str());
+        }
+    }
+    return batch_join(c);
+}
+
+int sub_elec(const msd_ctx* c, int s, int elec) { return elec % c->sub[s]->n_tot; }
+
+msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
+    for (int s = 0; s < n_systems; ++s) {
+        const msd_status st = validate(p + s);
+        if (st != MSD_OK) return fail(nullptr, st, "system %d: %s", s, g_init_error.c_str());
+    }
+    msd_ctx* c = new msd_ctx();
+    c->stream = static_cast<cudaStream_t>(p[0].cuda_stream);
+    c->mixed = p[0].prec == MSD_MIXED;
+    auto bail = [&](msd_status st) {
+        const std::string msg = c->err.empty() ? g_init_error : c->err;
+        msd_destroy(c);
+        g_init_error = msg;
+        return st;
+    };
+    const int ns = std::min(n_systems, kBatchStreams);
+    c->bstreams.assign(ns, nullptr);
+    c->bevents.assign(ns + 1, nullptr);
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamCreateWithFlags(&c->bstreams[i], cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(c, MSD_ERR_CUDA, "stream creation failed"));
+    for (int i = 0; i <= ns; ++i)
+        if (cudaEventCreateWithFlags(&c->bevents[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(c, MSD_ERR_CUDA, "event creation failed"));
+    long long w = 0, r = 0, d = 0, b = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        msd_problem q = p[s];
+        q.cuda_stream = c->bstreams[s % ns];
+        msd_ctx* sc = nullptr;
+        const msd_status st = msd_init(&q, 1, &sc);
+        if (st != MSD_OK) return bail(fail(c, st, "system %d: %s", s, g_init_error.c_str()));
+        c->sub.push_back(sc);
+        c->w_off.push_back(w);
+        c->r_off.push_back(r);
+        c->det_off.push_back(d);
+        c->b_off.push_back(b);
+        w += q.n_walkers;
+        r += 3LL * q.n_walkers * (q.n_elec[0] + q.n_elec[1]);
+        d += q.n_det;
+        b += (long long)q.n_basis * (q.n_orb[0] + q.n_orb[1]);
+    }
+    c->W = (int)w;
+    *out = c;
+    return MSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     g_init_error.clear();
     if (!out) return fail(nullptr, MSD_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (n_systems != 1)
-        return fail(nullptr, MSD_ERR_ARG, "n_systems = %d: this build handles one system per context", n_systems);
+    if (n_systems < 1) return fail(nullptr, MSD_ERR_ARG, "n_systems = %d must be >= 1", n_systems);
+    if (!p) return fail(nullptr, MSD_ERR_ARG, "problem is NULL");
+    if (n_systems > 1) return batch_init(p, n_systems, out);
     TRY(validate(p));
     msd_ctx* c = new msd_ctx();
     c->W = p->n_walkers;
@@ -639,6 +740,8 @@ msd_status msd_describe_records(const msd_problem* p, int32_t spin, uint8_t* out
 }
 
 msd_status msd_set_positions(msd_ctx* c, const double* R_dev) {
+    if (is_batch(c) && R_dev)
+        return batch_each(c, [&](int s, msd_ctx* sc) { return msd_set_positions(sc, R_dev + c->r_off[s]); });
     if (!c || !R_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     c->prop_valid = false;
     return set_positions(c, c->st, R_dev);
@@ -646,6 +749,12 @@ msd_status msd_set_positions(msd_ctx* c, const double* R_dev) {
 
 msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
                      double* lap_dev) {
+    if (is_batch(c) && rnew_dev && ratio_dev && elec >= 0)
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            const long long w = c->w_off[s];
+            return msd_ratio(sc, sub_elec(c, s, elec), rnew_dev + 3 * w, ratio_dev + w, grad_dev ? grad_dev + 3 * w : nullptr,
+                             lap_dev ? lap_dev + w : nullptr);
+        });
     if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if ((grad_dev == nullptr) != (lap_dev == nullptr))
@@ -681,6 +790,8 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
 }
 
 msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
+    if (is_batch(c) && accept_dev && elec >= 0)
+        return batch_each(c, [&](int s, msd_ctx* sc) { return msd_accept(sc, sub_elec(c, s, elec), accept_dev + c->w_off[s]); });
     if (!c || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (!c->prop_valid || c->prop_elec != elec)
         return fail(c, MSD_ERR_STATE, "msd_accept(%d) without a matching msd_ratio proposal", elec);
@@ -699,6 +810,13 @@ msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
 }
 
 msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev) {
+    if (is_batch(c) && grad_dev && lap_dev && elec >= -1)
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            // one electron: [W_s][3] per system; all electrons: [W_s][n_tot_s][3] per system
+            const long long go = elec >= 0 ? 3 * c->w_off[s] : c->r_off[s];
+            const long long lo = elec >= 0 ? c->w_off[s] : c->r_off[s] / 3;
+            return msd_grad_lap(sc, elec >= 0 ? sub_elec(c, s, elec) : -1, grad_dev + go, lap_dev + lo);
+        });
     if (!c || !grad_dev || !lap_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < -1 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
@@ -710,6 +828,12 @@ msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_
 
 msd_status msd_eval_batch(msd_ctx* c, const double* R_dev, double* logabs_dev, double* sign_dev, double* grad_dev,
                           double* lap_dev) {
+    if (is_batch(c) && R_dev && logabs_dev && sign_dev)
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            const long long w = c->w_off[s], r = c->r_off[s];
+            return msd_eval_batch(sc, R_dev + r, logabs_dev + w, sign_dev + w, grad_dev ? grad_dev + r : nullptr,
+                                  lap_dev ? lap_dev + r / 3 : nullptr);
+        });
     if (!c || !R_dev || !logabs_dev || !sign_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if ((grad_dev == nullptr) != (lap_dev == nullptr))
         return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
@@ -724,6 +848,12 @@ msd_status msd_eval_batch(msd_ctx* c, const double* R_dev, double* logabs_dev, d
 }
 
 msd_status msd_get_state(msd_ctx* c, double* R_dev, double* logabs_dev, double* sign_dev) {
+    if (is_batch(c))
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            const long long w = c->w_off[s];
+            return msd_get_state(sc, R_dev ? R_dev + c->r_off[s] : nullptr, logabs_dev ? logabs_dev + w : nullptr,
+                                 sign_dev ? sign_dev + w : nullptr);
+        });
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
     State& st = c->st;
@@ -738,6 +868,11 @@ msd_status msd_get_state(msd_ctx* c, double* R_dev, double* logabs_dev, double* 
 }
 
 msd_status msd_propose(msd_ctx* c, int32_t elec, const double* eta_dev, double tau, double* rnew_dev) {
+    if (is_batch(c) && eta_dev && rnew_dev && elec >= 0)
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            const long long w = c->w_off[s];
+            return msd_propose(sc, sub_elec(c, s, elec), eta_dev + 3 * w, tau, rnew_dev + 3 * w);
+        });
     if (!c || !eta_dev || !rnew_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
@@ -746,6 +881,11 @@ msd_status msd_propose(msd_ctx* c, int32_t elec, const double* eta_dev, double t
 }
 
 msd_status msd_metropolis(msd_ctx* c, const double* u_dev, const double* ratio_dev, uint8_t* accept_dev) {
+    if (is_batch(c) && u_dev && ratio_dev && accept_dev)
+        return batch_each(c, [&](int s, msd_ctx* sc) {
+            const long long w = c->w_off[s];
+            return msd_metropolis(sc, u_dev + w, ratio_dev + w, accept_dev + w);
+        });
     if (!c || !u_dev || !ratio_dev || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     launch_metropolis(c->L(), c->W, u_dev, ratio_dev, accept_dev);
     return check_launch(c, "metropolis");
@@ -753,6 +893,16 @@ msd_status msd_metropolis(msd_ctx* c, const double* u_dev, const double* ratio_d
 
 msd_status msd_ratio_host(msd_ctx* c, int32_t elec, const double* rnew_host, double* ratio_host, double* grad_host,
                           double* lap_host) {
+    if (is_batch(c) && rnew_host && ratio_host && elec >= 0) {
+        // host twins run system after system (each call is synchronous)
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            const long long w = c->w_off[q];
+            const msd_status st = msd_ratio_host(c->sub[q], sub_elec(c, (int)q, elec), rnew_host + 3 * w, ratio_host + w,
+                                                 grad_host ? grad_host + 3 * w : nullptr, lap_host ? lap_host + w : nullptr);
+            if (st != MSD_OK) return fail(c, st, "system %zu: %s", q, c->sub[q]->err.c_str());
+        }
+        return MSD_OK;
+    }
     if (!c || !rnew_host || !ratio_host) return fail(c, MSD_ERR_ARG, "NULL argument");
     if ((grad_host == nullptr) != (lap_host == nullptr))
         return fail(c, MSD_ERR_ARG, "grad_host and lap_host must be both NULL or both set");
@@ -775,6 +925,13 @@ msd_status msd_ratio_host(msd_ctx* c, int32_t elec, const double* rnew_host, dou
 }
 
 msd_status msd_accept_host(msd_ctx* c, int32_t elec, const uint8_t* accept_host) {
+    if (is_batch(c) && accept_host && elec >= 0) {
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            const msd_status st = msd_accept_host(c->sub[q], sub_elec(c, (int)q, elec), accept_host + c->w_off[q]);
+            if (st != MSD_OK) return fail(c, st, "system %zu: %s", q, c->sub[q]->err.c_str());
+        }
+        return MSD_OK;
+    }
     if (!c || !accept_host) return fail(c, MSD_ERR_ARG, "NULL argument");
     cudaError_t e = cudaMemcpyAsync(c->d_acc, accept_host, c->W, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
@@ -791,6 +948,15 @@ msd_status msd_set_stream(msd_ctx* c, void* stream) {
 }
 
 msd_status msd_sync(msd_ctx* c) {
+    if (is_batch(c)) {
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            const msd_status st = msd_sync(c->sub[q]);
+            if (st != MSD_OK) return fail(c, st, "system %zu: %s", q, c->sub[q]->err.c_str());
+        }
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        return MSD_OK;
+    }
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
@@ -811,6 +977,7 @@ const char* msd_last_error(const msd_ctx* c) {
 }
 
 msd_status msd_exc_histogram(const msd_ctx* c, int32_t spin, int64_t* out) {
+    if (is_batch(c)) return MSD_ERR_ARG;  // per system: query a single-system context
     if (!c || !out || spin < 0 || spin > 1) return MSD_ERR_ARG;
     out[0] = c->sp[spin].g.n_exc;
     for (int k = 0; k <= MAXK; ++k) out[1 + k] = c->sp[spin].hist[k];
@@ -818,6 +985,7 @@ msd_status msd_exc_histogram(const msd_ctx* c, int32_t spin, int64_t* out) {
 }
 
 msd_status msd_copy_state(msd_ctx* c, int32_t item, int32_t spin, void* dst, int64_t* bytes) {
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_copy_state takes a single-system context");
     if (!c || spin < 0 || spin > 1 || item < 0 || item > 11) return fail(c, MSD_ERR_ARG, "invalid argument");
     if (item >= 8) {
         if (c->prop_elec < 0) return fail(c, MSD_ERR_STATE, "no msd_ratio proposal yet");
@@ -852,6 +1020,10 @@ msd_status msd_copy_state(msd_ctx* c, int32_t item, int32_t spin, void* dst, int
 }
 
 msd_status msd_timing_start(msd_ctx* c) {
+    if (is_batch(c)) {
+        for (msd_ctx* sc : c->sub) TRY(msd_timing_start(sc));
+        return MSD_OK;
+    }
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     c->timing = true;
     c->launches = 0;
@@ -860,6 +1032,23 @@ msd_status msd_timing_start(msd_ctx* c) {
 }
 
 msd_status msd_timing_stop(msd_ctx* c, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches) {
+    if (is_batch(c)) {
+        // summed over systems (sweeps of different systems may overlap in time)
+        double ms = 0.0;
+        int64_t n1 = 0, n2 = 0;
+        for (msd_ctx* sc : c->sub) {
+            double a = 0.0;
+            int64_t b = 0, d = 0;
+            TRY(msd_timing_stop(sc, &a, &b, &d));
+            ms += a;
+            n1 += b;
+            n2 += d;
+        }
+        if (sweep_ms) *sweep_ms = ms;
+        if (sweep_launches) *sweep_launches = n1;
+        if (all_launches) *all_launches = n2;
+        return MSD_OK;
+    }
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
@@ -879,6 +1068,18 @@ msd_status msd_timing_stop(msd_ctx* c, double* sweep_ms, int64_t* sweep_launches
 }
 
 void msd_destroy(msd_ctx* c) {
+    if (c && !c->sub.empty()) {
+        for (msd_ctx* sc : c->sub) msd_destroy(sc);
+        c->sub.clear();
+    }
+    if (c) {
+        for (cudaStream_t st : c->bstreams)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : c->bevents)
+            if (ev) cudaEventDestroy(ev);
+        c->bstreams.clear();
+        c->bevents.clear();
+    }
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -888,6 +1089,8 @@ void msd_destroy(msd_ctx* c) {
 
 msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
                              double* lap_dev) {
+    if (is_batch(c))  // its scratch is one array per device: systems on concurrent streams would share it
+        return fail(c, MSD_ERR_ARG, "msd_ratio_noalloc takes a single-system context");
     if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if ((grad_dev == nullptr) != (lap_dev == nullptr))
@@ -919,6 +1122,10 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
 }
 
 msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, double* dB_dev) {
+    if (is_batch(c) && gbar_dev && dci_dev && dB_dev)
+        return batch_each(c, [&](int q, msd_ctx* sc) {
+            return msd_backward(sc, gbar_dev + c->w_off[q], dci_dev + c->det_off[q], dB_dev + c->b_off[q]);
+        });
     if (!c || !gbar_dev || !dci_dev || !dB_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
     for (int s = 0; s < 2; ++s) {

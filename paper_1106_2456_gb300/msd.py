@@ -335,3 +335,112 @@ class MSD:
         out = np.zeros(1 + 9, dtype=np.int64)
         self._check(self.lib.msd_exc_histogram(self.ctx, int(spin), out.ctypes.data))
         return out
+
+
+class MSDBatch:
+    """A libmsd context over several independent systems (msd_init with n_systems > 1).
+
+    Per-walker arrays are concatenations over systems; ``elec`` moves electron
+    elec mod n_tot_s of system s.  Only the calls a Metropolis driver and the adjoint need are
+    wrapped here; every other call of the C ABI works on the same context through ``lib``.
+    """
+
+    def __init__(self, problems, n_walkers, precision: str = "mixed", refresh_K=1 << 30,
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise MSDError(2, "a CUDA GPU is required (libmsd has no CPU path)")
+        self.lib = load_library()
+        self.problems = list(problems)
+        ns = len(self.problems)
+        Ws = list(n_walkers) if hasattr(n_walkers, "__len__") else [int(n_walkers)] * ns
+        Ks = list(refresh_K) if hasattr(refresh_K, "__len__") else [int(refresh_K)] * ns
+        self.Ws = [int(w) for w in Ws]
+        self.W = sum(self.Ws)
+        self.R_len = 3 * sum(w * p.n_tot for w, p in zip(self.Ws, self.problems))
+        self.n_det = sum(p.n_det for p in self.problems)
+        self.n_B = sum(p.n_basis * (p.n_orb[0] + p.n_orb[1]) for p in self.problems)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (_Problem * ns)()
+        self._keep = []
+        for i, (p, w, k) in enumerate(zip(self.problems, self.Ws, Ks)):
+            s, keep = problem_struct(p, w, precision, k, self.stream.cuda_stream)
+            arr[i] = s
+            self._keep.append(keep)
+        self._arr = arr
+        ctx = ctypes.c_void_p()
+        rc = self.lib.msd_init(ctypes.cast(arr, ctypes.c_void_p), ns, ctypes.byref(ctx))
+        if rc != 0:
+            raise MSDError(rc, self.lib.msd_last_error(None).decode())
+        self.ctx = ctx
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise MSDError(rc, self.lib.msd_last_error(self.ctx).decode())
+
+    def _empty(self, *shape, dtype=torch.float64):
+        return torch.empty(shape, dtype=dtype, device=self.dev)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.msd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, R: torch.Tensor):
+        """R: the concatenation of every system's [W_s, n_tot_s, 3] positions, flattened."""
+        self._check(self.lib.msd_set_positions(self.ctx, _dptr(R, torch.float64, (self.R_len,), "R")))
+
+    def propose(self, elec: int, eta: torch.Tensor, tau: float, out: torch.Tensor):
+        self._check(self.lib.msd_propose(self.ctx, int(elec), _dptr(eta, torch.float64, (self.W, 3), "eta"), float(tau),
+                                         _dptr(out, torch.float64, (self.W, 3), "rnew")))
+
+    def ratio_into(self, elec: int, rnew: torch.Tensor, ratio: torch.Tensor, grad: Optional[torch.Tensor] = None,
+                   lap: Optional[torch.Tensor] = None):
+        W = self.W
+        self._check(self.lib.msd_ratio(self.ctx, int(elec), _dptr(rnew, torch.float64, (W, 3), "rnew"),
+                                       _dptr(ratio, torch.float64, (W,), "ratio"),
+                                       _dptr(grad, torch.float64, (W, 3), "grad"),
+                                       _dptr(lap, torch.float64, (W,), "lap")))
+
+    def ratio(self, elec: int, rnew: torch.Tensor, with_grad: bool = True):
+        r = self._empty(self.W)
+        g = self._empty(self.W, 3) if with_grad else None
+        l = self._empty(self.W) if with_grad else None
+        self.ratio_into(elec, rnew, r, g, l)
+        return r, g, l
+
+    def metropolis(self, u: torch.Tensor, ratio: torch.Tensor, out: torch.Tensor):
+        self._check(self.lib.msd_metropolis(self.ctx, _dptr(u, torch.float64, (self.W,), "u"),
+                                            _dptr(ratio, torch.float64, (self.W,), "ratio"),
+                                            _dptr(out, torch.uint8, (self.W,), "accept")))
+
+    def accept(self, elec: int, accept: torch.Tensor):
+        self._check(self.lib.msd_accept(self.ctx, int(elec), _dptr(accept, torch.uint8, (self.W,), "accept")))
+
+    def get_state(self):
+        R, la, sg = self._empty(self.R_len), self._empty(self.W), self._empty(self.W)
+        self._check(self.lib.msd_get_state(self.ctx, R.data_ptr(), la.data_ptr(), sg.data_ptr()))
+        return R, la, sg
+
+    def backward(self, gbar: torch.Tensor):
+        dci, dB = self._empty(self.n_det), self._empty(self.n_B)
+        self._check(self.lib.msd_backward(self.ctx, _dptr(gbar, torch.float64, (self.W,), "gbar"), dci.data_ptr(),
+                                          dB.data_ptr()))
+        return dci, dB
+
+    def sync(self):
+        self._check(self.lib.msd_sync(self.ctx))
+
+    def timing_start(self):
+        self._check(self.lib.msd_timing_start(self.ctx))
+
+    def timing_stop(self):
+        ms, n1, n2 = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.msd_timing_stop(self.ctx, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
+        return ms.value, n1.value, n2.value

@@ -329,6 +329,36 @@ def make_workload(label: str, n_walkers: Optional[int] = None, n_det: Optional[i
                     n_sweeps=cfg["sweeps"], label=label)
 
 
+def feasible_terms(n: int, m: int, kmin: int, kmax: int) -> int:
+    """Distinct (up string, down string) pairs of total excitation order kmin..kmax."""
+    a = [math.comb(n, r) * math.comb(m, r) if r <= min(n, m, MAXK) else 0 for r in range(kmax + 1)]
+    return sum(a[ru] * a[r - ru] for r in range(kmin, kmax + 1) for ru in range(r + 1))
+
+
+def batched_workloads(n_systems: int = 256, W: int = 256, seed: int = 1004, n_range=(4, 96),
+                      det_range=(1e2, 1e5), kmax: int = 6, K: int = 64, tau: float = 0.5) -> List[Workload]:
+    """Independent systems of uneven size: n per spin uniform in n_range, N = 3 n orbitals,
+    n_det log-uniform in det_range (capped at a quarter of the distinct terms that orders
+    1..kmax allow, so small systems stay drawable), orders geometric on 1..kmax,
+    max(3, ceil(n / 8)) nuclei on a chain, W walkers each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_systems):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        N = 3 * n
+        nd = int(round(math.exp(rng.uniform(math.log(det_range[0]), math.log(det_range[1])))))
+        nd = max(1, min(nd, feasible_terms(n, N - n, 1, kmax) // 4))
+        sub_seed = int(rng.integers(1 << 30))
+        srng = np.random.default_rng(sub_seed)
+        nuc = chain_nuclei(srng, max(3, -(-n // 8)))
+        prob = make_problem(sub_seed, nuc, (n, n), (N, N), nd, geometric_orders(1, kmax), rng=srng,
+                            name=f"batch{i}")
+        R0 = initial_walkers(srng, nuc, prob.n_tot, W)
+        out.append(Workload(problem=prob, R0=R0, tau=tau, seed=sub_seed, n_walkers=W, refresh_K=K, n_sweeps=1,
+                            label=f"batch{i}"))
+    return out
+
+
 def custom_workload(n: Tuple[int, int], N: Tuple[int, int], n_det: int, orders: Dict[int, float],
                     W: int, n_nuc: int = 3, seed: int = 7, tau: float = 0.5, K: int = 1 << 30,
                     label: str = "custom") -> Workload:

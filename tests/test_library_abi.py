@@ -116,11 +116,34 @@ def test_init_rejects_bad_strings(lib):
     assert rc == 1
 
 
-def test_init_rejects_batched_systems(lib):
+def test_init_batched_validation(lib):
+    """n_systems > 1 reads an array of problems and validates each before any CUDA call."""
     w = wl.make_workload("water", n_walkers=4)
-    s, keep = _struct(w.problem)
-    rc, msg = _init_status(lib, s, n_systems=3)
+    rc, msg = _init_status(lib, _struct(w.problem)[0], n_systems=0)
     assert rc == 1 and "n_systems" in msg
+    keep = []
+    arr = (msd._Problem * 3)()
+    for i in range(3):
+        s, k = _struct(w.problem)
+        keep.append(k)
+        arr[i] = s
+    arr[2].refresh_K = 0
+    ctx = ctypes.c_void_p()
+    rc = lib.msd_init(ctypes.cast(arr, ctypes.c_void_p), 3, ctypes.byref(ctx))
+    msg = lib.msd_last_error(None).decode()
+    assert rc == 1 and "system 2" in msg and "refresh_K" in msg and not ctx.value
+
+
+def test_batched_workloads_shapes():
+    ws = wl.batched_workloads(12, W=3, seed=5)
+    for w in ws:
+        p = w.problem
+        n = p.n_elec[0]
+        assert 4 <= n <= 96 and p.n_elec == (n, n) and p.n_orb == (3 * n, 3 * n)
+        assert 1 <= p.n_det <= max(1, wl.feasible_terms(n, 2 * n, 1, 6) // 4)
+        assert p.exc_orders(0).max() <= 6 and w.R0.shape == (3, 2 * n, 3)
+    # the small-system cap: 4 electrons per spin, 8 virtuals
+    assert wl.feasible_terms(4, 8, 1, 6) == 208764
 
 
 def test_init_rejects_table_larger_than_shared_memory(lib):
