@@ -227,6 +227,16 @@ msd_status msd_timing_stop(msd_ctx* ctx, double* sweep_ms, int64_t* sweep_launch
  * one SM's shared memory. */
 msd_status msd_backward(msd_ctx* ctx, const double* gbar_dev, double* dci_dev, double* dB_dev);
 
+/* Replace the wavefunction's parameters from HOST arrays, then rebuild the state at the
+ * current positions (as msd_set_positions does).  ci_host [n_det] (NULL keeps the CI
+ * coefficients); B_up_host [n_basis][n_orb[0]] and B_dn_host [n_basis][n_orb[1]] (both NULL
+ * keeps the orbital coefficients, both or neither).  A batched context takes ci and B
+ * concatenated per system as msd_backward returns them (B_dn_host is then ignored).  Drops a
+ * pending msd_ratio proposal.  Synchronises the context's stream.  With msd_backward this is
+ * what a parameter optimisation needs (the paper optimises the CI coefficients in Sec. VI
+ * with its own tools). */
+msd_status msd_set_params(msd_ctx* ctx, const double* ci_host, const double* B_up_host, const double* B_dn_host);
+
 /* msd_ratio without any device allocation and without keeping a proposal (the paper has no
  * counterpart: it is a library concern).  Same arguments and results as msd_ratio for the
  * current state, but the orbitals at rnew_dev go to a fixed device array of 4 MiB inside the

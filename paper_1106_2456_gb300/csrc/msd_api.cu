@@ -39,6 +39,7 @@ struct SpinConst {
     std::vector<uint8_t> h_rec;
     std::vector<int> h_toff, h_tother, h_heavy;
     std::vector<double> h_tc;
+    std::vector<int> h_tpos;      // term I -> its slot in the term lists of this spin (kept)
 };
 
 struct State {
@@ -399,11 +400,13 @@ msd_status plan_terms(SpinConst& S, const SpinConst& O, const msd_problem* p, in
     std::vector<int> pos(off.begin(), off.end() - 1);
     std::vector<int> other(nd);
     std::vector<double> cc(nd);
+    S.h_tpos.assign(nd, 0);
     for (int64_t I = 0; I < nd; ++I) {
         const int u = S.internal_of[mine[I]];
         const int q = pos[u]++;
         other[q] = O.internal_of[oth[I]];
         cc[q] = p->ci[I];
+        S.h_tpos[I] = q;
     }
     std::vector<int> heavy;
     for (int u = 0; u < ne; ++u)
@@ -496,10 +499,18 @@ msd_status recompute_S(msd_ctx* c, State& st, int s) {
     return check_launch(c, "CI sum");
 }
 
+msd_status rebuild(msd_ctx* c, State& st);
+
 msd_status set_positions(msd_ctx* c, State& st, const double* R_dev) {
     cudaError_t e = cudaMemcpyAsync(st.R, R_dev, sizeof(double) * c->W * c->n_tot * 3, cudaMemcpyDeviceToDevice,
                                     c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of positions: %s", cudaGetErrorString(e));
+    return rebuild(c, st);
+}
+
+// Everything from scratch at the positions in st.R (Section III: inverse and determinants
+// "calculated from scratch").
+msd_status rebuild(msd_ctx* c, State& st) {
     TRY(refresh_spin(c, st, 0));
     TRY(refresh_spin(c, st, 1));
     st.C_valid[0] = st.C_valid[1] = false;
@@ -1164,6 +1175,50 @@ msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, dou
         dB += (size_t)c->nb * S.N;
     }
     return check_launch(c, "backward");
+}
+
+msd_status msd_set_params(msd_ctx* c, const double* ci_host, const double* B_up_host, const double* B_dn_host) {
+    if (is_batch(c)) {
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            const msd_ctx* sc = c->sub[q];
+            const double* b = B_up_host ? B_up_host + c->b_off[q] : nullptr;
+            const double* bd = b ? b + (size_t)sc->nb * sc->sp[0].N : nullptr;
+            const msd_status st =
+                msd_set_params(c->sub[q], ci_host ? ci_host + c->det_off[q] : nullptr, b, bd);
+            if (st != MSD_OK) return fail(c, st, "system %zu: %s", q, c->sub[q]->err.c_str());
+        }
+        return MSD_OK;
+    }
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    if ((B_up_host == nullptr) != (B_dn_host == nullptr))
+        return fail(c, MSD_ERR_ARG, "B_up_host and B_dn_host must be both NULL or both set");
+    if (ci_host)
+        for (long long I = 0; I < c->n_det; ++I)
+            if (!std::isfinite(ci_host[I])) return fail(c, MSD_ERR_ARG, "ci[%lld] not finite", I);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+        SpinConst& S = c->sp[s];
+        if (ci_host) {
+            std::vector<double> cc(c->n_det);
+            for (long long I = 0; I < c->n_det; ++I) cc[S.h_tpos[I]] = ci_host[I];
+            e = cudaMemcpy(S.t_c, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice);
+        }
+        if (B_up_host && e == cudaSuccess) {
+            const double* Bh = s ? B_dn_host : B_up_host;
+            const size_t cnt = (size_t)c->nb * S.N;
+            if (c->mixed) {
+                std::vector<float> b32(Bh, Bh + cnt);
+                e = cudaMemcpy(S.B, b32.data(), sizeof(float) * cnt, cudaMemcpyHostToDevice);
+            } else {
+                e = cudaMemcpy(S.B, Bh, sizeof(double) * cnt, cudaMemcpyHostToDevice);
+            }
+        }
+    }
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "parameter upload: %s", cudaGetErrorString(e));
+    c->prop_valid = false;
+    c->scratch.C_valid[0] = c->scratch.C_valid[1] = false;
+    if (!c->st.ready) return MSD_OK;
+    return rebuild(c, c->st);
 }
 
 }  // extern "C"

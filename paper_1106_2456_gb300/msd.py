@@ -86,6 +86,7 @@ def load_library():
         "msd_accept": ([vp, i32, vp], i32),
         "msd_ratio_noalloc": ([vp, i32, vp, vp, vp, vp], i32),
         "msd_backward": ([vp, vp, vp, vp], i32),
+        "msd_set_params": ([vp, vp, vp, vp], i32),
         "msd_grad_lap": ([vp, i32, vp, vp], i32),
         "msd_eval_batch": ([vp, vp, vp, vp, vp, vp], i32),
         "msd_get_state": ([vp, vp, vp, vp], i32),
@@ -235,6 +236,22 @@ class MSD:
                                                _dptr(ratio, torch.float64, (W,), "ratio"),
                                                _dptr(grad, torch.float64, (W, 3), "grad"),
                                                _dptr(lap, torch.float64, (W,), "lap")))
+
+    def set_params(self, ci: Optional[np.ndarray] = None, B: Optional[Tuple[np.ndarray, np.ndarray]] = None):
+        """msd_set_params: new CI coefficients [n_det] and/or orbital coefficients (B_up, B_dn),
+        host arrays; the state is rebuilt at the current positions."""
+        c = None if ci is None else np.ascontiguousarray(ci, dtype=np.float64)
+        if c is not None and c.shape != (self.p.n_det,):
+            raise ValueError(f"ci: expected shape ({self.p.n_det},)")
+        b0 = b1 = None
+        if B is not None:
+            b0 = np.ascontiguousarray(B[0], dtype=np.float64)
+            b1 = np.ascontiguousarray(B[1], dtype=np.float64)
+            if b0.shape != (self.p.n_basis, self.p.n_orb[0]) or b1.shape != (self.p.n_basis, self.p.n_orb[1]):
+                raise ValueError("B: expected shapes (n_basis, n_orb[s])")
+        self._check(self.lib.msd_set_params(self.ctx, None if c is None else c.ctypes.data,
+                                            None if b0 is None else b0.ctypes.data,
+                                            None if b1 is None else b1.ctypes.data))
 
     def backward(self, gbar: torch.Tensor):
         """msd_backward: (dci [n_det], (dB_up [n_basis, n_orb_up], dB_dn [n_basis, n_orb_dn])) of
