@@ -172,6 +172,31 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_inputs(wl, rank: int, total: int):
+    """Walker positions and Metropolis streams of one replica: rank 0 runs the workload's own
+    seeds, rank r > 0 offset seeds and positions jittered by 0.01 bohr (independent chains)."""
+    rng = np.random.default_rng(4242 + rank)
+    R0 = wl.R0 + (0.01 * rng.standard_normal(wl.R0.shape) if rank else 0.0)
+    eta, u = wl.proposals(total, seed_offset=rank)
+    return R0, eta, u
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest replica's)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(walkers_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job walker-moves per second: every replica's walkers over the slowest time."""
+    return walkers_per_rank * world * steps / seconds
+
+
 # ----------------------------------------------------------------------------------------
 # the oracle arm (CPU, FP64, every determinant by LU)
 # ----------------------------------------------------------------------------------------
@@ -259,10 +284,8 @@ def run_ours(args):
     n_tot = p.n_tot
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    rng = np.random.default_rng(4242 + rank)
-    R0 = wl.R0 + (0.01 * rng.standard_normal(wl.R0.shape) if rank else 0.0)
     total = args.warmup + args.steps
-    eta_np, u_np = wl.proposals(total, seed_offset=rank)
+    R0, eta_np, u_np = replica_inputs(wl, rank, total)
     eta = torch.tensor(eta_np, device=dev)
     u = torch.tensor(u_np, device=dev)
 
@@ -305,11 +328,7 @@ def run_ours(args):
         sweep_ms, n_sweep, n_launch = c.timing_stop()
         if clk:
             clk.stop()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         c.sync()
         return ms, sweep_ms, n_sweep, n_launch, (clk.summary(w0, w1) if clk else None)
 
@@ -347,7 +366,7 @@ def run_ours(args):
     # ---- mixed precision (headline) ----
     cm = make("mixed")
     ms, sweep_ms, n_sweep, n_launch, clocks = timed(cm, args.steps)
-    value = W * ws * args.steps / (ms * 1e-3)
+    value = job_rate(W, ws, args.steps, ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -379,12 +398,8 @@ def run_ours(args):
             cm.accept_host(e, acc_h)
             sel = acc_h.astype(bool)
             Rh[sel, e] = rnew_h[sel]
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([dt], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        line["e2e"] = {"value": W * ws * e2e_steps / dt, "unit": UNIT, "steps": e2e_steps,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        line["e2e"] = {"value": job_rate(W, ws, e2e_steps, dt), "unit": UNIT, "steps": e2e_steps,
                        "h2d_bytes_per_step": W * 3 * 8 + W, "d2h_bytes_per_step": W * 5 * 8,
                        "path": "msd_ratio_host + msd_accept_host (pinned host buffers, synchronous)"}
     # ---- FP64 path on the same workload ----
@@ -393,7 +408,7 @@ def run_ours(args):
         cd = make("fp64")
         steps64 = min(args.steps, args.fp64_steps)
         ms64, sweep64, _, _, clk64 = timed(cd, steps64)
-        line["fp64"] = {"value": W * ws * steps64 / (ms64 * 1e-3), "ms_per_step": ms64 / steps64, "steps": steps64,
+        line["fp64"] = {"value": job_rate(W, ws, steps64, ms64 * 1e-3), "ms_per_step": ms64 / steps64, "steps": steps64,
                         "roofline": roofline("fp64", sweep64, steps64), "clocks": clk64}
         line["mixed_speedup_vs_fp64"] = value / line["fp64"]["value"]
         # per-result difference mixed vs FP64 on a common trajectory (FP64 accept decisions)

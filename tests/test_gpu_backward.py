@@ -100,3 +100,18 @@ def test_backward_identities_medium():
     tol = 1e-10 * max(kappa, 10.0)
     assert e_c <= tol and e_B <= tol, (e_c, e_B, kappa)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_backward_differentiation_config(prec):
+    """The differentiation workload's shape (32 + 32 electrons, 160 orbitals per spin, 5e4
+    determinants, orders 1-6): the adjoint of 2 walkers against the oracle."""
+    wk = wl.make_workload("diff", n_walkers=2)
+    p = wk.problem
+    ctx = msd.MSD(p, wk.n_walkers, prec, refresh_K=wk.refresh_K)
+    ctx.set_positions(torch.tensor(wk.R0, device="cuda"))
+    gbar = np.array([1.0, -0.7])
+    e_c, e_B, kappa = _errors(ctx, p, wk.R0, gbar)
+    tol = (1e-10 if prec == "fp64" else 1e3 * 2.0 ** -24) * max(kappa, 10.0)
+    assert e_c <= tol and e_B <= tol, (e_c, e_B, kappa)
+    ctx.close()
