@@ -232,14 +232,29 @@ def workload_desc(name, wl):
             f"per GPU, refresh every {wl.refresh_K} steps of a spin")
 
 
+def batched_desc(systems, walkers_per_system):
+    dets = sum(w.problem.n_det for w in systems)
+    ns = [w.problem.n_elec[0] for w in systems]
+    return (f"batched: {len(systems)} systems, n per spin {min(ns)}-{max(ns)}, N = 3n, {dets} determinants in total "
+            f"(log-uniform 1e2-1e5 per system, orders 1-6), {walkers_per_system} walkers per system "
+            f"({walkers_per_system * len(systems)} per GPU)")
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     from paper_1106_2456_gb300 import workloads
 
-    full = workloads.make_workload(args.workload, **({"n_walkers": args.walkers} if args.walkers else {}))
-    wl = workloads.make_workload(args.workload, n_walkers=2)
+    if args.workload == "batched":
+        # the oracle on the largest system of the batch (its slowest single-walker moves)
+        systems = workloads.batched_workloads(args.systems, W=2, seed=1004)
+        desc = batched_desc(systems, args.walkers or 256)
+        wl = max(systems, key=lambda w: w.problem.n_det * w.problem.n_elec[0] ** 3)
+    else:
+        full = workloads.make_workload(args.workload, **({"n_walkers": args.walkers} if args.walkers else {}))
+        desc = workload_desc(args.workload, full)
+        wl = workloads.make_workload(args.workload, n_walkers=2)
     warm = min(args.warmup, 1)
     if warm:
         oracle_rate(wl, warm, 60.0)
@@ -249,7 +264,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws, "steps": done,
             "warmup": warm, "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload, full), "walkers_per_step": 1,
+            "config": {"workload": desc, "walkers_per_step": 1,
                        "precision": "fp64 (oracle: every determinant by LU)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -260,6 +275,118 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 # the CUDA arm
 # ----------------------------------------------------------------------------------------
+def run_batched(args):
+    """Batched uneven systems (one context over many systems): walker-moves/s of all systems."""
+    import torch
+
+    from paper_1106_2456_gb300 import msd, workloads
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    msd.load_library()
+    peaks, peak_kind = load_peaks()
+    systems = workloads.batched_workloads(args.systems, W=args.walkers or 256, seed=1004)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    W = sum(w.n_walkers for w in systems)
+    total = args.warmup + args.steps
+    rng = np.random.default_rng(77 + rank)
+    eta = torch.tensor(rng.standard_normal((total, W, 3)), device=dev)
+    u = torch.tensor(rng.random((total, W)), device=dev)
+    R0 = torch.tensor(np.concatenate([w.R0.reshape(-1) for w in systems]), device=dev)
+    bufs = dict(rnew=torch.empty(W, 3, dtype=torch.float64, device=dev),
+                ratio=torch.empty(W, dtype=torch.float64, device=dev),
+                grad=torch.empty(W, 3, dtype=torch.float64, device=dev),
+                lap=torch.empty(W, dtype=torch.float64, device=dev),
+                acc=torch.empty(W, dtype=torch.uint8, device=dev))
+
+    def run(prec, steps):
+        b = msd.MSDBatch([w.problem for w in systems], [w.n_walkers for w in systems], prec,
+                         refresh_K=[w.refresh_K for w in systems], stream=stream)
+        b.set_positions(R0)
+
+        def step(t):
+            b.propose(t, eta[t], 0.5, bufs["rnew"])
+            b.ratio_into(t, bufs["rnew"], bufs["ratio"], bufs["grad"], bufs["lap"])
+            b.metropolis(u[t], bufs["ratio"], bufs["acc"])
+            b.accept(t, bufs["acc"])
+
+        for t in range(args.warmup):
+            step(t)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clk = ClockSampler(local) if rank == 0 else None
+        time.sleep(0.3 if clk else 0)
+        b.timing_start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        e0.record(stream)
+        for t in range(args.warmup, args.warmup + steps):
+            step(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        sweep_ms, n_sweep, n_launch = b.timing_stop()
+        if clk:
+            clk.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        b.sync()
+        b.close()
+        # algorithmic work of every system's sweeps in these steps
+        F = B = 0.0
+        for w in systems:
+            p = w.problem
+            plan = msd.describe(p, prec)
+            for t in range(args.warmup, args.warmup + steps):
+                sp = p.spin_of(t % p.n_tot)
+                f, by = sweep_work(p, sp, w.n_walkers, prec == "mixed", int(plan[sp][0]))
+                F += f
+                B += by
+        return ms, sweep_ms, n_sweep, n_launch, F, B, (clk.summary(w0, w1) if clk else None)
+
+    ms, sweep_ms, n_sweep, n_launch, F, B, clocks = run("mixed", args.steps)
+    sec = ms * 1e-3
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    hbm = {"achieved": B / sec / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": B / sec / 1e9 / hbm_peak,
+           "peak_source": peak_kind}
+    alu = {"achieved": F / sec / 1e12, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+           "frac": F / sec / 1e12 / FP32_ALU_TFLOPS, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    bound_alu = F / (FP32_ALU_TFLOPS * 1e12) >= B / (hbm_peak * 1e9)
+    roof = dict(alu if bound_alu else hbm)
+    roof.update(bound="alu" if bound_alu else "hbm", traffic=None,
+                kernel="k_ratio of every system (launches of different systems overlap): sweep work per step / "
+                       "step time",
+                launches=int(n_sweep), other=hbm if bound_alu else alu)
+    line = {"metric": METRIC, "value": job_rate(W, ws, args.steps, sec), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": batched_desc(systems, W // len(systems)),
+                       "precision": "mixed", "parallelism": f"replicas x{ws}, systems on 8 streams",
+                       "l2": "inputs exceed L2"},
+            "roofline": roof, "gpu_launches": int(n_launch), "clocks": clocks}
+    if not args.skip_fp64:
+        steps64 = min(args.steps, args.fp64_steps)
+        ms64, _, _, _, _, _, clk64 = run("fp64", steps64)
+        line["fp64"] = {"value": job_rate(W, ws, steps64, ms64 * 1e-3), "ms_per_step": ms64 / steps64,
+                        "steps": steps64, "clocks": clk64}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -462,11 +589,14 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--walkers", type=int, default=0, help="override the workload's walker count (profiling)")
+    ap.add_argument("--systems", type=int, default=256, help="systems of the batched workload")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 
