@@ -340,7 +340,13 @@ def run_batched(args):
         if clk:
             clk.stop()
         ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        b.sync()
+        # a walker whose reference matrix becomes nearly singular (Section V) can drive the FP32
+        # path to a non-finite ratio; the library flags it and the run goes on: report it
+        try:
+            b.sync()
+            flagged = None
+        except msd.MSDError as ex:
+            flagged = str(ex)
         b.close()
         # algorithmic work of every system's sweeps in these steps
         F = B = 0.0
@@ -352,9 +358,9 @@ def run_batched(args):
                 f, by = sweep_work(p, sp, w.n_walkers, prec == "mixed", int(plan[sp][0]))
                 F += f
                 B += by
-        return ms, sweep_ms, n_sweep, n_launch, F, B, (clk.summary(w0, w1) if clk else None)
+        return ms, sweep_ms, n_sweep, n_launch, F, B, (clk.summary(w0, w1) if clk else None), flagged
 
-    ms, sweep_ms, n_sweep, n_launch, F, B, clocks = run("mixed", args.steps)
+    ms, sweep_ms, n_sweep, n_launch, F, B, clocks, flagged = run("mixed", args.steps)
     sec = ms * 1e-3
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     hbm = {"achieved": B / sec / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": B / sec / 1e9 / hbm_peak,
@@ -373,12 +379,12 @@ def run_batched(args):
             "config": {"workload": batched_desc(systems, W // len(systems)),
                        "precision": "mixed", "parallelism": f"replicas x{ws}, systems on 8 streams",
                        "l2": "inputs exceed L2"},
-            "roofline": roof, "gpu_launches": int(n_launch), "clocks": clocks}
+            "roofline": roof, "gpu_launches": int(n_launch), "clocks": clocks, "status": flagged or "ok"}
     if not args.skip_fp64:
         steps64 = min(args.steps, args.fp64_steps)
-        ms64, _, _, _, _, _, clk64 = run("fp64", steps64)
+        ms64, _, _, _, _, _, clk64, flagged64 = run("fp64", steps64)
         line["fp64"] = {"value": job_rate(W, ws, steps64, ms64 * 1e-3), "ms_per_step": ms64 / steps64,
-                        "steps": steps64, "clocks": clk64}
+                        "steps": steps64, "clocks": clk64, "status": flagged64 or "ok"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
