@@ -79,65 +79,101 @@ __device__ __forceinline__ void copy_to_smem(TT* dst, const TT* __restrict__ src
 // A1: basis functions and orbitals at a set of points
 // ------------------------------------------------------------------------------------------
 // chi_mu(r) = (r - A)_c^l exp(-alpha |r - A|^2) with its gradient and laplacian, then
-// phi^a_j = sum_mu chi^a_mu B[mu][j] (Algorithm 1 step 2).  PB points per block; phase 1
-// fills chi in shared memory, phase 2 streams B once per block and contracts.
-template <typename TO, int NC, int PB>
-__global__ void __launch_bounds__(128) k_orbitals(int P, int ppw, const double* __restrict__ pos,
-                                                  long long wstride, int p_off, const double4* __restrict__ bas,
-                                                  const int8_t* __restrict__ blm, int nb,
-                                                  const TO* __restrict__ B, int N, TO* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    TO* chi = reinterpret_cast<TO*>(smem);  // [nb][PB * NC]
-    const int p0 = blockIdx.x * PB;
-    for (int idx = threadIdx.x; idx < PB * nb; idx += blockDim.x) {
-        const int q = idx / nb, mu = idx - q * nb;
-        const int p = p0 + q;
-        TO v[5] = {TO(0), TO(0), TO(0), TO(0), TO(0)};
-        if (p < P) {
-            const int w = p / ppw, r = p - w * ppw;
-            const double* rp = pos + (long long)w * wstride + (long long)(p_off + r) * 3;
-            const double4 b = bas[mu];
-            const TO d[3] = {TO(rp[0] - b.x), TO(rp[1] - b.y), TO(rp[2] - b.z)};
-            const TO al = TO(b.w);
-            const TO d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            const TO g = texp(-al * d2);
-            const int lm = blm[mu];
-            if (lm == 0) {
-                v[0] = g;
-                v[1] = TO(-2) * al * d[0] * g;
-                v[2] = TO(-2) * al * d[1] * g;
-                v[3] = TO(-2) * al * d[2] * g;
-                v[4] = (TO(4) * al * al * d2 - TO(6) * al) * g;
-            } else {
-                const int c = lm - 1;
-                const TO dc = d[c];
-                v[0] = dc * g;
+// phi^a_j = sum_mu chi^a_mu B[mu][j] (Algorithm 1 step 2): a [P NC x nb] x [nb x N] product
+// whose left factor is generated on the fly.  Block tile: kOrbTP points x kOrbTJ orbitals, all
+// NC channels; basis functions in chunks of KC, the chunk of chi (every point and channel) and
+// of B staged in shared memory; each thread accumulates 2 points x NC channels x 4 orbitals.
+constexpr int kOrbTP = 32;
+constexpr int kOrbTJ = 64;
+
+template <typename TO>
+__device__ __forceinline__ void basis_channels(const double* rp, double4 b, int lm, TO (&v)[5]) {
+    const TO d[3] = {TO(rp[0] - b.x), TO(rp[1] - b.y), TO(rp[2] - b.z)};
+    const TO al = TO(b.w);
+    const TO d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const TO g = texp(-al * d2);
+    if (lm == 0) {
+        v[0] = g;
+        v[1] = TO(-2) * al * d[0] * g;
+        v[2] = TO(-2) * al * d[1] * g;
+        v[3] = TO(-2) * al * d[2] * g;
+        v[4] = (TO(4) * al * al * d2 - TO(6) * al) * g;
+    } else {
+        const int c = lm - 1;
+        const TO dc = d[c];
+        v[0] = dc * g;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) v[1 + a] = ((a == c ? TO(1) : TO(0)) - TO(2) * al * d[a] * dc) * g;
-                v[4] = dc * (TO(4) * al * al * d2 - TO(10) * al) * g;
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < NC; ++a) chi[mu * (PB * NC) + q * NC + a] = v[a];
+        for (int a = 0; a < 3; ++a) v[1 + a] = ((a == c ? TO(1) : TO(0)) - TO(2) * al * d[a] * dc) * g;
+        v[4] = dc * (TO(4) * al * al * d2 - TO(10) * al) * g;
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        TO acc[PB * NC];
+}
+
+template <typename TO>
+constexpr int orb_kc() {
+    return sizeof(TO) == 4 ? 48 : 24;
+}
+
+template <typename TO, int NC>
+__global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* __restrict__ pos, long long wstride,
+                                                  int p_off, const double4* __restrict__ bas,
+                                                  const int8_t* __restrict__ blm, int nb, const TO* __restrict__ B,
+                                                  int N, TO* __restrict__ out) {
+    constexpr int KC = orb_kc<TO>();
+    __shared__ __align__(16) TO chi[KC][kOrbTP * NC];
+    __shared__ __align__(16) TO Bs[KC][kOrbTJ];
+    const int p0 = blockIdx.x * kOrbTP, j0 = blockIdx.y * kOrbTJ;
+    const int tid = threadIdx.x, pg = tid >> 4, jg = tid & 15;  // points 2 pg, 2 pg + 1; orbitals 4 jg .. 4 jg + 3
+    TO acc[2][NC][4];
 #pragma unroll
-        for (int q = 0; q < PB * NC; ++q) acc[q] = TO(0);
-        for (int mu = 0; mu < nb; ++mu) {
-            const TO bj = __ldg(B + (long long)mu * N + j);
-            const TO* cr = chi + mu * (PB * NC);
+    for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int q = 0; q < PB * NC; ++q) acc[q] = fma(cr[q], bj, acc[q]);
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[q][a][c] = TO(0);
+    for (int k0 = 0; k0 < nb; k0 += KC) {
+        const int kc = min(KC, nb - k0);
+        for (int idx = tid; idx < kOrbTP * KC; idx += blockDim.x) {
+            // consecutive threads take consecutive points: their chi stores fall in distinct banks
+            const int kk = idx / kOrbTP, q = idx - kk * kOrbTP, p = p0 + q, mu = k0 + kk;
+            TO v[5] = {TO(0), TO(0), TO(0), TO(0), TO(0)};
+            if (p < P && kk < kc) {
+                const int w = p / ppw, r = p - w * ppw;
+                basis_channels<TO>(pos + (long long)w * wstride + (long long)(p_off + r) * 3, bas[mu], blm[mu], v);
+            }
+#pragma unroll
+            for (int a = 0; a < NC; ++a) chi[kk][q * NC + a] = v[a];
         }
-#pragma unroll
-        for (int q = 0; q < PB; ++q) {
-            const int p = p0 + q;
-            if (p < P)
-#pragma unroll
-                for (int a = 0; a < NC; ++a) out[((long long)p * NC + a) * N + j] = acc[q * NC + a];
+        for (int idx = tid; idx < KC * kOrbTJ; idx += blockDim.x) {
+            const int kk = idx / kOrbTJ, jj = idx - kk * kOrbTJ, j = j0 + jj;
+            Bs[kk][jj] = (kk < kc && j < N) ? __ldg(B + (long long)(k0 + kk) * N + j) : TO(0);
         }
+        __syncthreads();
+        for (int kk = 0; kk < kc; ++kk) {
+            TO b[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][4 * jg + c];
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const TO x = chi[kk][(2 * pg + q) * NC + a];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][a][c] = fma(x, b[c], acc[q][a][c]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int p = p0 + 2 * pg + q;
+        if (p >= P) continue;
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + 4 * jg + c;
+                if (j < N) out[((long long)p * NC + a) * N + j] = acc[q][a][c];
+            }
     }
 }
 
@@ -768,22 +804,13 @@ void set_smem(Kern kern, size_t bytes) {
 template <typename TO>
 static void orbitals_impl(const Launch& L, int nch, int P, int ppw, const double* pos, long long wstride, int p_off,
                           const double4* bas, const int8_t* blm, int nb, const TO* B, int N, TO* out) {
-    if (P <= 0) return;
-    if (nch == 5) {
-        constexpr int PB = 8;
-        const size_t sm = (size_t)nb * PB * 5 * sizeof(TO);
-        set_smem(k_orbitals<TO, 5, PB>, sm);
-        L.count();
-        k_orbitals<TO, 5, PB><<<(P + PB - 1) / PB, 128, sm, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B,
-                                                                         N, out);
-    } else {
-        constexpr int PB = 16;
-        const size_t sm = (size_t)nb * PB * sizeof(TO);
-        set_smem(k_orbitals<TO, 1, PB>, sm);
-        L.count();
-        k_orbitals<TO, 1, PB><<<(P + PB - 1) / PB, 128, sm, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B,
-                                                                         N, out);
-    }
+    if (P <= 0 || N <= 0) return;
+    const dim3 grid((P + kOrbTP - 1) / kOrbTP, (N + kOrbTJ - 1) / kOrbTJ);
+    L.count();
+    if (nch == 5)
+        k_orbitals<TO, 5><<<grid, 256, 0, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B, N, out);
+    else
+        k_orbitals<TO, 1><<<grid, 256, 0, L.stream>>>(P, ppw, pos, wstride, p_off, bas, blm, nb, B, N, out);
 }
 
 void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const double* pos, long long wstride,
