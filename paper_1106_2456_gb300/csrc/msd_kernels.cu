@@ -725,9 +725,12 @@ __global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict
     if (!a.accept[w]) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, m = a.m, tid = threadIdx.x, bd = blockDim.x;
+    // np partial sums per entry of v so that all threads share the n-term FP64 dot products
+    const int np = bd >= 2 * n ? bd / n : 1;
     double* xr = reinterpret_cast<double*>(smem);  // [n] x[c] / rho
     double* pd = xr + n;                           // [n] phi_occ(r')
     double* v = pd + n;                            // [n]
+    double* vp = v + n;                            // [np][n] partial sums
     double* Aw = a.Ainv + (long long)w * n * n;
     const TO* phw = static_cast<const TO*>(a.phi) + (long long)w * a.nch * a.N;
     const double rho = a.rho[w];
@@ -737,10 +740,25 @@ __global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict
         pd[c] = double(phw[c]);
     }
     __syncthreads();
-    for (int r = tid; r < n; r += bd) {
-        double acc = 0.0;
-        for (int c = 0; c < n; ++c) acc = fma(pd[c], Aw[(long long)c * n + r], acc);
-        v[r] = acc - (r == a.row ? 1.0 : 0.0);
+    if (np > 1) {
+        const int r = tid % n, part = tid / n;
+        if (part < np) {
+            double acc = 0.0;
+            for (int c = part; c < n; c += np) acc = fma(pd[c], Aw[(long long)c * n + r], acc);
+            vp[part * n + r] = acc;
+        }
+        __syncthreads();
+        for (int r2 = tid; r2 < n; r2 += bd) {
+            double acc = 0.0;
+            for (int q = 0; q < np; ++q) acc += vp[q * n + r2];
+            v[r2] = acc - (r2 == a.row ? 1.0 : 0.0);
+        }
+    } else {
+        for (int r = tid; r < n; r += bd) {
+            double acc = 0.0;
+            for (int c = 0; c < n; ++c) acc = fma(pd[c], Aw[(long long)c * n + r], acc);
+            v[r] = acc - (r == a.row ? 1.0 : 0.0);
+        }
     }
     __syncthreads();
     const int lane = tid & 31, nw = bd >> 5;
@@ -751,10 +769,30 @@ __global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict
     }
     TT* Tw = static_cast<TT*>(a.T) + (long long)w * n * m;
     const TT* yw = static_cast<const TT*>(a.y0) + (long long)w * m;
-    for (int c = tid >> 5; c < n; c += nw) {
-        TT* row = Tw + (long long)c * m;
-        const TT xc = TT(xr[c]);
-        for (int av = lane; av < m; av += 32) row[av] = fma(xc, yw[av], row[av]);
+    const bool vec = sizeof(TT) == 4 && (m & 3) == 0 && ((reinterpret_cast<uintptr_t>(Tw) | reinterpret_cast<uintptr_t>(yw)) & 15) == 0;
+    if (vec) {
+        // FP32 rows as float4: m / 4 vectors per row, one row per warp at a time
+        const int m4 = m >> 2;
+        const float4* y4 = reinterpret_cast<const float4*>(yw);
+        for (int c = tid >> 5; c < n; c += nw) {
+            float4* row = reinterpret_cast<float4*>(Tw + (long long)c * m);
+            const float xc = float(xr[c]);
+            for (int q = lane; q < m4; q += 32) {
+                float4 t = row[q];
+                const float4 y = y4[q];
+                t.x = fmaf(xc, y.x, t.x);
+                t.y = fmaf(xc, y.y, t.y);
+                t.z = fmaf(xc, y.z, t.z);
+                t.w = fmaf(xc, y.w, t.w);
+                row[q] = t;
+            }
+        }
+    } else {
+        for (int c = tid >> 5; c < n; c += nw) {
+            TT* row = Tw + (long long)c * m;
+            const TT xc = TT(xr[c]);
+            for (int av = lane; av < m; av += 32) row[av] = fma(xc, yw[av], row[av]);
+        }
     }
     if (tid == 0) {
         if (!(rho != 0.0) || !isfinite(rho)) atomicOr(status, ST_SINGULAR);
@@ -944,7 +982,8 @@ void launch_ratio(const Launch& L, bool mixed, const RatioArgs& a) {
 }
 
 void launch_accept(const Launch& L, bool mixed, const AcceptArgs& a) {
-    const size_t sm = (size_t)a.n * 3 * 8;
+    const int np = kBlock >= 2 * a.n ? kBlock / a.n : 1;
+    const size_t sm = (size_t)a.n * (3 + np) * 8;
     L.count();
     if (mixed) k_accept<float, float><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
     else k_accept<double, double><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
