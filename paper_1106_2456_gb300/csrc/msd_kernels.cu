@@ -449,6 +449,10 @@ __global__ void __launch_bounds__(kBlock) k_ci_dot(int n_exc, const TT* __restri
 // are five length-m dot products afterwards.  Singles are a dense n x m block when most are
 // present: G1[p] = sum_h C1[h][p] x[h], S_T += sum_{h,p} C1[h][p] T[h][p].
 constexpr int kWarps = kBlock / 32;
+#ifndef MSD_SWEEP_DEPTH
+#define MSD_SWEEP_DEPTH 2
+#endif
+constexpr int kSweepDepth = MSD_SWEEP_DEPTH;  // batches of loads in flight per warp
 
 template <int K, typename TT, int NGW>
 __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int ld, const TT* xs,
@@ -461,19 +465,33 @@ __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int l
     // `base` on, so the batches left over at the end of a group fall on different warps.
     const int nb = (j1 - j0) / kBatch;
     int b = (warp - ((j0 - base) / kBatch) % nw + nw) % nw;
-    // two batches of record and C loads in flight ahead of the arithmetic
+    // kSweepDepth batches of record and C loads in flight ahead of the arithmetic
     using Raw = typename RecRaw<K>::type;
-    Raw r0{}, r1{};
-    TT c0 = TT(0), c1 = TT(0);
-    if (b < nb) { r0 = load_raw<K>(rec, b * kBatch + lane); c0 = __ldcs(Cw + j0 + b * kBatch + lane); }
-    if (b + nw < nb) { r1 = load_raw<K>(rec, (b + nw) * kBatch + lane); c1 = __ldcs(Cw + j0 + (b + nw) * kBatch + lane); }
+    Raw rq[kSweepDepth];
+    TT cq[kSweepDepth];
+#pragma unroll
+    for (int i = 0; i < kSweepDepth; ++i) {
+        const int bi = b + i * nw;
+        rq[i] = Raw{};
+        cq[i] = TT(0);
+        if (bi < nb) {
+            rq[i] = load_raw<K>(rec, bi * kBatch + lane);
+            cq[i] = __ldcs(Cw + j0 + bi * kBatch + lane);
+        }
+    }
     for (; b < nb; b += nw) {
-        const Raw rc = r0;
-        const TT cu = c0;
-        r0 = r1;
-        c0 = c1;
-        const int bn = b + 2 * nw;
-        if (bn < nb) { r1 = load_raw<K>(rec, bn * kBatch + lane); c1 = __ldcs(Cw + j0 + bn * kBatch + lane); }
+        const Raw rc = rq[0];
+        const TT cu = cq[0];
+#pragma unroll
+        for (int i = 0; i + 1 < kSweepDepth; ++i) {
+            rq[i] = rq[i + 1];
+            cq[i] = cq[i + 1];
+        }
+        const int bn = b + kSweepDepth * nw;
+        if (bn < nb) {
+            rq[kSweepDepth - 1] = load_raw<K>(rec, bn * kBatch + lane);
+            cq[kSweepDepth - 1] = __ldcs(Cw + j0 + bn * kBatch + lane);
+        }
         int h[K], p[K];
         decode_rec<K>(rc, h, p);
         if (h[0] != kEmptyRecord) {
