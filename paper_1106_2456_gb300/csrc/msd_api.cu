@@ -90,9 +90,12 @@ struct msd_ctx {
     // batched uneven systems: one single-system context per system, run on kBatchStreams
     // internal streams forked from and joined back into `stream`
     std::vector<msd_ctx*> sub;
+    std::vector<msd_ctx*> sub_parked;  // (timing: lets the batch context reuse the single-system code)
     std::vector<long long> w_off, r_off, det_off, b_off;  // per system: walkers, positions, terms, B entries
     std::vector<cudaStream_t> bstreams;
     std::vector<cudaEvent_t> bevents;                       // [0] fork, [1 + i] join of stream i
+    BatchPlan bplan;                                        // single-launch descriptors of the systems
+    double* b_rnew = nullptr;                               // [W][3] positions of the current proposal
     std::vector<void*> allocs;
     std::string err;
     // measurement: kernel launch count and events around the excitation-sweep kernel
@@ -587,6 +590,160 @@ msd_status batch_each(msd_ctx* c, F&& f) {
 
 int sub_elec(const msd_ctx* c, int s, int elec) { return elec % c->sub[s]->n_tot; }
 
+// Descriptors of every system for the single-launch stages (orbitals at r', ratio, accept,
+// proposal): pointers into each system's own context, per spin.
+msd_status build_batch_plan(msd_ctx* c) {
+    const int ns = (int)c->sub.size();
+    std::vector<BatchSys> sys(ns);
+    std::vector<int4> tiles;
+    std::vector<int> wsys;
+    std::vector<size_t> sys_smem(ns, 0);
+    size_t rsm = 0, asm_ = 0;
+    const int TP = orbital_tile_points(), TJ = orbital_tile_orbitals();
+    for (int q = 0; q < ns; ++q) {
+        msd_ctx* sc = c->sub[q];
+        BatchSys& B = sys[q];
+        B.n_tot = sc->n_tot;
+        B.n_up = sc->sp[0].n;
+        B.W = sc->W;
+        B.w_off = (int)c->w_off[q];
+        B.status = sc->d_status;
+        B.R = sc->st.R;
+        int Nmax = 0;
+        for (int s = 0; s < 2; ++s) {
+            const SpinConst& S = sc->sp[s];
+            B.orb[s] = OrbArgs{sc->bas, sc->blm, sc->nb, S.B, S.N, sc->phi_new};
+            RatioArgs& a = B.ratio[s];
+            a = RatioArgs{};
+            a.W = sc->W; a.n = S.n; a.N = S.N; a.m = S.m;
+            a.phi = sc->phi_new; a.Ainv = sc->st.Ainv[s]; a.T = sc->st.T[s]; a.C = sc->st.C[s]; a.S = sc->st.S;
+            a.g = S.g;
+            if (S.m == 0) a.g.kmax = 0;
+            a.rho = sc->rho; a.num = sc->num; a.y0 = sc->y0;
+            AcceptArgs& b = B.accept[s];
+            b = AcceptArgs{};
+            b.W = sc->W; b.n = S.n; b.N = S.N; b.m = S.m; b.n_tot = sc->n_tot;
+            b.phi = sc->phi_new; b.rho = sc->rho; b.num = sc->num; b.y0 = sc->y0;
+            b.Ainv = sc->st.Ainv[s]; b.T = sc->st.T[s]; b.R = sc->st.R; b.logdet = sc->st.logdet[s];
+            b.sgn = sc->st.sgn[s]; b.S = sc->st.S;
+            sys_smem[q] = std::max(sys_smem[q], ratio_smem_bytes(c->mixed, S.n, S.m, NCH));
+            rsm = std::max(rsm, sys_smem[q]);
+            asm_ = std::max(asm_, accept_smem_bytes(S.n));
+            Nmax = std::max(Nmax, S.N);
+        }
+        for (int w = 0; w < sc->W; ++w) wsys.push_back(q);
+        for (int p0 = 0; p0 < sc->W; p0 += TP)
+            for (int j0 = 0; j0 < Nmax; j0 += TJ) tiles.push_back(make_int4(q, p0, j0, 0));
+    }
+    // ratio blocks grouped by shared-memory size class (the CTAs an SM can hold), largest last
+    auto cls = [&](size_t sm) {
+        const size_t per_sm = 227 * 1024;
+        const int fit = (int)std::min<size_t>(3, per_sm / (sm + 1024));
+        return fit >= 3 ? 0 : fit == 2 ? 1 : 2;
+    };
+    std::vector<int2> blk;
+    BatchPlan& P = c->bplan;
+    P.n_groups = 0;
+    for (int g = 0; g < 3; ++g) {
+        const int first = (int)blk.size();
+        size_t gs = 0;
+        for (int q = 0; q < ns; ++q) {
+            if (cls(sys_smem[q]) != g) continue;
+            gs = std::max(gs, sys_smem[q]);
+            for (int w = 0; w < c->sub[q]->W; ++w) blk.push_back(make_int2(q, w));
+        }
+        if ((int)blk.size() == first) continue;
+        P.gfirst[P.n_groups] = first;
+        P.gsmem[P.n_groups] = gs;
+        P.n_groups++;
+        P.gfirst[P.n_groups] = (int)blk.size();
+    }
+    BatchSys* d_sys = nullptr;
+    int2* d_blk = nullptr;
+    int4* d_tiles = nullptr;
+    int* d_wsys = nullptr;
+    TRY(upload(c, &d_sys, sys.data(), sys.size()));
+    TRY(upload(c, &d_blk, blk.data(), blk.size()));
+    TRY(upload(c, &d_tiles, tiles.data(), tiles.size()));
+    TRY(upload(c, &d_wsys, wsys.data(), wsys.size()));
+    TRY(dalloc(c, &c->b_rnew, (size_t)c->W * 3));
+    c->bplan.sys = d_sys;
+    c->bplan.n_sys = ns;
+    c->bplan.blk = d_blk;
+    c->bplan.n_blk = (int)blk.size();
+    c->bplan.tiles = d_tiles;
+    c->bplan.n_tiles = (int)tiles.size();
+    c->bplan.wsys = d_wsys;
+    c->bplan.ratio_smem = rsm;
+    c->bplan.accept_smem = asm_;
+    return MSD_OK;
+}
+
+// Per-system bookkeeping of a batched msd_ratio (refresh, CI weights: launched on the internal
+// streams between a fork and a join when a system needs them), then one launch each for the
+// orbitals at r' and the ratio of every system.
+msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
+                       double* lap_dev) {
+    if ((grad_dev == nullptr) != (lap_dev == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
+    const int nch = grad_dev ? NCH : 1;
+    bool forked = false;
+    for (size_t q = 0; q < c->sub.size(); ++q) {
+        msd_ctx* sc = c->sub[q];
+        State& st = sc->st;
+        if (!st.ready) return fail(c, MSD_ERR_STATE, "system %zu: msd_set_positions has not been called", q);
+        const int e = elec % sc->n_tot, s = spin_of(sc, e);
+        const bool refresh = st.since_refresh[s] >= sc->K;
+        if (refresh || !st.C_valid[s]) {
+            if (!forked) {
+                TRY(batch_fork(c));
+                forked = true;
+            }
+            msd_status r = MSD_OK;
+            if (refresh) {
+                r = refresh_spin(sc, st, s);
+                if (r == MSD_OK) r = ensure_C(sc, st, s);
+                if (r == MSD_OK) r = recompute_S(sc, st, s);
+            } else {
+                r = ensure_C(sc, st, s);
+            }
+            if (r != MSD_OK) {
+                batch_join(c);
+                return fail(c, r, "system %zu: %s", q, sc->err.c_str());
+            }
+        }
+        st.since_refresh[s]++;
+        sc->prop_elec = e;
+        sc->prop_nch = nch;
+        sc->prop_valid = true;
+    }
+    if (forked) TRY(batch_join(c));
+    const cudaError_t e = cudaMemcpyAsync(c->b_rnew, rnew_dev, sizeof(double) * 3 * c->W, cudaMemcpyDeviceToDevice,
+                                          c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
+    launch_orbitals_batched(c->L(), c->mixed, c->bplan, elec, nch, c->b_rnew);
+    launch_ratio_batched(c->L_sweep(), c->mixed, c->bplan, elec, nch, ratio_dev, grad_dev, lap_dev);
+    return check_launch(c, "batched ratio");
+}
+
+msd_status batch_accept(msd_ctx* c, int elec, const uint8_t* accept_dev) {
+    int nch = 0;
+    for (size_t q = 0; q < c->sub.size(); ++q) {
+        msd_ctx* sc = c->sub[q];
+        const int e = elec % sc->n_tot;
+        if (!sc->prop_valid || sc->prop_elec != e)
+            return fail(c, MSD_ERR_STATE, "system %zu: msd_accept(%d) without a matching msd_ratio proposal", q, elec);
+        nch = sc->prop_nch;
+    }
+    for (msd_ctx* sc : c->sub) {
+        const int s = spin_of(sc, elec % sc->n_tot);
+        sc->st.C_valid[1 - s] = false;
+        sc->prop_valid = false;
+    }
+    launch_accept_batched(c->L(), c->mixed, c->bplan, elec, nch, accept_dev, c->b_rnew);
+    return check_launch(c, "batched accept");
+}
+
 msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
     for (int s = 0; s < n_systems; ++s) {
         const msd_status st = validate(p + s);
@@ -628,6 +785,7 @@ msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
         b += (long long)q.n_basis * (q.n_orb[0] + q.n_orb[1]);
     }
     c->W = (int)w;
+    if (build_batch_plan(c) != MSD_OK) return bail(MSD_ERR_CUDA);
     *out = c;
     return MSD_OK;
 }
@@ -760,12 +918,7 @@ msd_status msd_set_positions(msd_ctx* c, const double* R_dev) {
 
 msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
                      double* lap_dev) {
-    if (is_batch(c) && rnew_dev && ratio_dev && elec >= 0)
-        return batch_each(c, [&](int s, msd_ctx* sc) {
-            const long long w = c->w_off[s];
-            return msd_ratio(sc, sub_elec(c, s, elec), rnew_dev + 3 * w, ratio_dev + w, grad_dev ? grad_dev + 3 * w : nullptr,
-                             lap_dev ? lap_dev + w : nullptr);
-        });
+    if (is_batch(c) && rnew_dev && ratio_dev && elec >= 0) return batch_ratio(c, elec, rnew_dev, ratio_dev, grad_dev, lap_dev);
     if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if ((grad_dev == nullptr) != (lap_dev == nullptr))
@@ -801,8 +954,7 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
 }
 
 msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
-    if (is_batch(c) && accept_dev && elec >= 0)
-        return batch_each(c, [&](int s, msd_ctx* sc) { return msd_accept(sc, sub_elec(c, s, elec), accept_dev + c->w_off[s]); });
+    if (is_batch(c) && accept_dev && elec >= 0) return batch_accept(c, elec, accept_dev);
     if (!c || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (!c->prop_valid || c->prop_elec != elec)
         return fail(c, MSD_ERR_STATE, "msd_accept(%d) without a matching msd_ratio proposal", elec);
@@ -879,11 +1031,10 @@ msd_status msd_get_state(msd_ctx* c, double* R_dev, double* logabs_dev, double* 
 }
 
 msd_status msd_propose(msd_ctx* c, int32_t elec, const double* eta_dev, double tau, double* rnew_dev) {
-    if (is_batch(c) && eta_dev && rnew_dev && elec >= 0)
-        return batch_each(c, [&](int s, msd_ctx* sc) {
-            const long long w = c->w_off[s];
-            return msd_propose(sc, sub_elec(c, s, elec), eta_dev + 3 * w, tau, rnew_dev + 3 * w);
-        });
+    if (is_batch(c) && eta_dev && rnew_dev && elec >= 0) {
+        launch_propose_batched(c->L(), c->bplan, c->W, elec, eta_dev, tau, rnew_dev);
+        return check_launch(c, "batched proposal");
+    }
     if (!c || !eta_dev || !rnew_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
@@ -892,11 +1043,10 @@ msd_status msd_propose(msd_ctx* c, int32_t elec, const double* eta_dev, double t
 }
 
 msd_status msd_metropolis(msd_ctx* c, const double* u_dev, const double* ratio_dev, uint8_t* accept_dev) {
-    if (is_batch(c) && u_dev && ratio_dev && accept_dev)
-        return batch_each(c, [&](int s, msd_ctx* sc) {
-            const long long w = c->w_off[s];
-            return msd_metropolis(sc, u_dev + w, ratio_dev + w, accept_dev + w);
-        });
+    if (is_batch(c) && u_dev && ratio_dev && accept_dev) {
+        launch_metropolis(c->L(), c->W, u_dev, ratio_dev, accept_dev);  // elementwise over all walkers
+        return check_launch(c, "metropolis");
+    }
     if (!c || !u_dev || !ratio_dev || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     launch_metropolis(c->L(), c->W, u_dev, ratio_dev, accept_dev);
     return check_launch(c, "metropolis");
@@ -1031,10 +1181,8 @@ msd_status msd_copy_state(msd_ctx* c, int32_t item, int32_t spin, void* dst, int
 }
 
 msd_status msd_timing_start(msd_ctx* c) {
-    if (is_batch(c)) {
-        for (msd_ctx* sc : c->sub) TRY(msd_timing_start(sc));
-        return MSD_OK;
-    }
+    if (is_batch(c))
+        for (msd_ctx* sc : c->sub) TRY(msd_timing_start(sc));  // their own bookkeeping launches; then ours
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     c->timing = true;
     c->launches = 0;
@@ -1043,10 +1191,16 @@ msd_status msd_timing_start(msd_ctx* c) {
 }
 
 msd_status msd_timing_stop(msd_ctx* c, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches) {
-    if (is_batch(c)) {
-        // summed over systems (sweeps of different systems may overlap in time)
-        double ms = 0.0;
-        int64_t n1 = 0, n2 = 0;
+    if (is_batch(c) && c->timing) {
+        // the single-launch stages (this context's events) plus the systems' own launches
+        double own = 0.0;
+        int64_t o1 = 0, o2 = 0;
+        c->sub.swap(c->sub_parked);
+        const msd_status st0 = msd_timing_stop(c, &own, &o1, &o2);
+        c->sub.swap(c->sub_parked);
+        TRY(st0);
+        double ms = own;
+        int64_t n1 = o1, n2 = o2;
         for (msd_ctx* sc : c->sub) {
             double a = 0.0;
             int64_t b = 0, d = 0;

@@ -126,6 +126,52 @@ void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, 
 
 size_t ratio_smem_bytes(bool mixed, int n, int m, int nch);
 
+// Batched systems in single launches: per-system descriptors (device), built by the host at
+// initialisation.  A kernel reads its system, derives the moving electron e = t mod n_tot and
+// its spin, and runs the single-system per-block code on that system's arrays.
+struct OrbArgs {
+    const double4* bas;
+    const int8_t* blm;
+    int nb;
+    const void* B;   // [nb][N] of the spin
+    int N;
+    void* out;       // [W][nch][N] orbitals at the proposed positions
+};
+struct BatchSys {
+    int n_tot, n_up, W, w_off;  // electrons, walkers, offset of the walkers in concatenated arrays
+    int* status;                // the system's status word
+    const double* R;            // [W][n_tot][3]
+    OrbArgs orb[2];             // per spin
+    RatioArgs ratio[2];         // per spin, without row, nch and outputs
+    AcceptArgs accept[2];       // per spin, without row, elec, nch, accept flags and rnew
+};
+struct BatchPlan {
+    const BatchSys* sys = nullptr;
+    int n_sys = 0;
+    const int2* blk = nullptr;  // ratio and accept blocks: (system, walker), grouped by ratio_groups
+    int n_blk = 0;
+    // ratio launches: blocks [gfirst[i], gfirst[i + 1]) share a shared-memory size gsmem[i], so
+    // small systems are not held to the occupancy of the largest one
+    static constexpr int kMaxGroups = 4;
+    int n_groups = 0;
+    int gfirst[kMaxGroups + 1] = {0};
+    size_t gsmem[kMaxGroups] = {0};
+    const int4* tiles = nullptr;  // orbital tiles: (system, first point, first orbital, -)
+    int n_tiles = 0;
+    const int* wsys = nullptr;  // system of each concatenated walker
+    size_t ratio_smem = 0, accept_smem = 0;
+};
+void launch_orbitals_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const double* rnew);
+void launch_ratio_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, double* ratio, double* grad,
+                          double* lap);
+void launch_accept_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const uint8_t* accept,
+                           const double* rnew);
+void launch_propose_batched(const Launch& L, const BatchPlan& P, int W_total, int t, const double* eta, double tau,
+                            double* rnew);
+size_t accept_smem_bytes(int n);
+int orbital_tile_points();
+int orbital_tile_orbitals();
+
 // Adjoint of log|Psi| (msd_backward.cu).  dci[I] += sum_w gbar[w] t0[w][iu[I]] t1[w][id[I]] / S[w].
 void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* iu, const int* id, const double* gbar,
                 const double* S, const void* t0, int ld0, const void* t1, int ld1, double* dci);

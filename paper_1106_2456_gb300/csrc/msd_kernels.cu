@@ -114,14 +114,13 @@ constexpr int orb_kc() {
 }
 
 template <typename TO, int NC>
-__global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* __restrict__ pos, long long wstride,
-                                                  int p_off, const double4* __restrict__ bas,
-                                                  const int8_t* __restrict__ blm, int nb, const TO* __restrict__ B,
-                                                  int N, TO* __restrict__ out) {
+__device__ __forceinline__ void orbitals_tile(int P, int ppw, const double* __restrict__ pos, long long wstride,
+                                              int p_off, const double4* __restrict__ bas,
+                                              const int8_t* __restrict__ blm, int nb, const TO* __restrict__ B, int N,
+                                              TO* __restrict__ out, const int p0, const int j0) {
     constexpr int KC = orb_kc<TO>();
     __shared__ __align__(16) TO chi[KC][kOrbTP * NC];
     __shared__ __align__(16) TO Bs[KC][kOrbTJ];
-    const int p0 = blockIdx.x * kOrbTP, j0 = blockIdx.y * kOrbTJ;
     const int tid = threadIdx.x, pg = tid >> 4, jg = tid & 15;  // points 2 pg, 2 pg + 1; orbitals 4 jg .. 4 jg + 3
     TO acc[2][NC][4];
 #pragma unroll
@@ -175,6 +174,15 @@ __global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* 
                 if (j < N) out[((long long)p * NC + a) * N + j] = acc[q][a][c];
             }
     }
+}
+
+template <typename TO, int NC>
+__global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* __restrict__ pos, long long wstride,
+                                                  int p_off, const double4* __restrict__ bas,
+                                                  const int8_t* __restrict__ blm, int nb, const TO* __restrict__ B,
+                                                  int N, TO* __restrict__ out) {
+    orbitals_tile<TO, NC>(P, ppw, pos, wstride, p_off, bas, blm, nb, B, N, out, blockIdx.x * kOrbTP,
+                          blockIdx.y * kOrbTJ);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -574,8 +582,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // and y^0 itself only when the proposal is kept for msd_accept.  FP32 tables reduce across a
 // warp in FP32 and across warps in FP64.
 template <typename TO, typename TT, int NC>
-__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
-    k_ratio(RatioArgs a, int* __restrict__ status) {
+__device__ __forceinline__ void ratio_block(const RatioArgs& a, const int w, int* __restrict__ status) {
     constexpr int NGW = ratio_ngw<TT>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, m = a.m, N = a.N;
@@ -590,7 +597,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
     double* red = reinterpret_cast<double*>(smem + L.red);
     __shared__ double s_s[NC];
 
-    const int w = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int tid = threadIdx.x, bd = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (m > 0) cp_async_block(Ts, static_cast<const TT*>(a.T) + (long long)w * n * m, (size_t)n * m * sizeof(TT));
     const TO* phw = static_cast<const TO*>(a.phi) + (long long)w * NC * N;
@@ -733,13 +740,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
     }
 }
 
+template <typename TO, typename TT, int NC>
+__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
+    k_ratio(const __grid_constant__ RatioArgs a, int* __restrict__ status) {
+    ratio_block<TO, TT, NC>(a, blockIdx.x, status);
+}
+
 // ------------------------------------------------------------------------------------------
 // A6: accept -- Sherman-Morrison update of A_0^{-1} (FP64), rank-1 update of T (Section III)
 // ------------------------------------------------------------------------------------------
 // Ainv' = Ainv - x v^T / rho with v = phi_occ(r')^T Ainv - e_i^T, T' = T + x y^T / rho.
 template <typename TO, typename TT>
-__global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict__ status) {
-    const int w = blockIdx.x;
+__device__ __forceinline__ void accept_block(const AcceptArgs& a, const int w, int* __restrict__ status) {
     if (!a.accept[w]) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, m = a.m, tid = threadIdx.x, bd = blockDim.x;
@@ -821,6 +833,11 @@ __global__ void __launch_bounds__(kBlock) k_accept(AcceptArgs a, int* __restrict
     }
 }
 
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBlock) k_accept(const __grid_constant__ AcceptArgs a, int* __restrict__ status) {
+    accept_block<TO, TT>(a, blockIdx.x, status);
+}
+
 __global__ void k_propose(int W, int n_tot, int elec, const double* __restrict__ R, const double* __restrict__ eta,
                           double tau, double* __restrict__ rnew) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -845,6 +862,85 @@ __global__ void k_state(int W, const double* __restrict__ ld0, const double* __r
     const double s = S[w];
     if (logabs) logabs[w] = ld0[w] + ld1[w] + log(fabs(s));
     if (sign) sign[w] = sg0[w] * sg1[w] * (s < 0.0 ? -1.0 : (s > 0.0 ? 1.0 : 0.0));
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched systems: one launch per stage for every system (per-system descriptors)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int batch_spin(const BatchSys& B, int t, int& e) {
+    e = t % B.n_tot;
+    return e < B.n_up ? 0 : 1;
+}
+
+template <typename TO, int NC>
+__global__ void __launch_bounds__(256) k_orbitals_batched(const BatchSys* __restrict__ sys, const int4* __restrict__ tiles,
+                                                          int t, const double* __restrict__ rnew) {
+    const int4 tl = tiles[blockIdx.x];
+    const BatchSys& B = sys[tl.x];
+    int e;
+    const OrbArgs& o = B.orb[batch_spin(B, t, e)];
+    if (tl.z >= o.N) return;  // tile beyond this spin's orbitals (uniform over the block)
+    orbitals_tile<TO, NC>(B.W, 1, rnew + 3LL * B.w_off, 3, 0, o.bas, o.blm, o.nb, static_cast<const TO*>(o.B), o.N,
+                          static_cast<TO*>(o.out), tl.y, tl.z);
+}
+
+template <typename TO, typename TT, int NC>
+__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
+    k_ratio_batched(const BatchSys* __restrict__ sys, const int2* __restrict__ blk, int t, double* ratio,
+                    double* grad, double* lap) {
+    __shared__ RatioArgs sa;
+    __shared__ int* s_status;
+    const int2 bw = blk[blockIdx.x];  // blk already offset to this launch's group
+    if (threadIdx.x == 0) {
+        const BatchSys& B = sys[bw.x];
+        int e;
+        const int sp = batch_spin(B, t, e);
+        sa = B.ratio[sp];
+        sa.row = e - (sp ? B.n_up : 0);
+        sa.nch = NC;
+        sa.ratio = ratio + B.w_off;
+        sa.rs = 1;
+        sa.grad = grad ? grad + 3LL * B.w_off : nullptr;
+        sa.gs = 3;
+        sa.lap = lap ? lap + B.w_off : nullptr;
+        sa.ls = 1;
+        s_status = B.status;
+    }
+    __syncthreads();
+    ratio_block<TO, TT, NC>(sa, bw.y, s_status);
+}
+
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBlock) k_accept_batched(const BatchSys* __restrict__ sys, const int2* __restrict__ blk,
+                                                           int t, int nch, const uint8_t* __restrict__ accept,
+                                                           const double* __restrict__ rnew) {
+    __shared__ AcceptArgs sa;
+    __shared__ int* s_status;
+    const int2 bw = blk[blockIdx.x];
+    if (threadIdx.x == 0) {
+        const BatchSys& B = sys[bw.x];
+        int e;
+        const int sp = batch_spin(B, t, e);
+        sa = B.accept[sp];
+        sa.row = e - (sp ? B.n_up : 0);
+        sa.elec = e;
+        sa.nch = nch;
+        sa.accept = accept + B.w_off;
+        sa.rnew = rnew + 3LL * B.w_off;
+        s_status = B.status;
+    }
+    __syncthreads();
+    accept_block<TO, TT>(sa, bw.y, s_status);
+}
+
+__global__ void k_propose_batched(const BatchSys* __restrict__ sys, const int* __restrict__ wsys, int Wt, int t,
+                                  const double* __restrict__ eta, double tau, double* __restrict__ rnew) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Wt * 3) return;
+    const int gw = i / 3, d = i - gw * 3;
+    const BatchSys& B = sys[wsys[gw]];
+    const int w = gw - B.w_off, e = t % B.n_tot;
+    rnew[i] = fma(tau, eta[i], B.R[((long long)w * B.n_tot + e) * 3 + d]);
 }
 
 template <typename Kern>
@@ -1000,8 +1096,7 @@ void launch_ratio(const Launch& L, bool mixed, const RatioArgs& a) {
 }
 
 void launch_accept(const Launch& L, bool mixed, const AcceptArgs& a) {
-    const int np = kBlock >= 2 * a.n ? kBlock / a.n : 1;
-    const size_t sm = (size_t)a.n * (3 + np) * 8;
+    const size_t sm = accept_smem_bytes(a.n);
     L.count();
     if (mixed) k_accept<float, float><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
     else k_accept<double, double><<<a.W, kBlock, sm, L.stream>>>(a, L.status);
@@ -1058,5 +1153,70 @@ cudaError_t noalloc_scratch(void** ptr) {
     *ptr = addr[dev];
     return cudaSuccess;
 }
+
+template <typename TO>
+static void orbitals_batched_impl(const Launch& L, const BatchPlan& P, int t, int nch, const double* rnew) {
+    if (P.n_tiles <= 0) return;
+    L.count();
+    if (nch == 5)
+        k_orbitals_batched<TO, 5><<<P.n_tiles, 256, 0, L.stream>>>(P.sys, P.tiles, t, rnew);
+    else
+        k_orbitals_batched<TO, 1><<<P.n_tiles, 256, 0, L.stream>>>(P.sys, P.tiles, t, rnew);
+}
+
+void launch_orbitals_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const double* rnew) {
+    if (mixed) orbitals_batched_impl<float>(L, P, t, nch, rnew);
+    else orbitals_batched_impl<double>(L, P, t, nch, rnew);
+}
+
+template <typename TO, typename TT>
+static void ratio_batched_impl(const Launch& L, const BatchPlan& P, int t, int nch, double* ratio, double* grad,
+                               double* lap) {
+    if (L.t0) cudaEventRecord(L.t0, L.stream);
+    set_smem(k_ratio_batched<TO, TT, 5>, P.ratio_smem);
+    set_smem(k_ratio_batched<TO, TT, 1>, P.ratio_smem);
+    for (int g = 0; g < P.n_groups; ++g) {
+        const int nb = P.gfirst[g + 1] - P.gfirst[g];
+        if (nb <= 0) continue;
+        L.count();
+        if (nch == 5)
+            k_ratio_batched<TO, TT, 5><<<nb, kBlock, P.gsmem[g], L.stream>>>(P.sys, P.blk + P.gfirst[g], t, ratio,
+                                                                             grad, lap);
+        else
+            k_ratio_batched<TO, TT, 1><<<nb, kBlock, P.gsmem[g], L.stream>>>(P.sys, P.blk + P.gfirst[g], t, ratio,
+                                                                             grad, lap);
+    }
+    if (L.t1) cudaEventRecord(L.t1, L.stream);
+}
+
+void launch_ratio_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, double* ratio, double* grad,
+                          double* lap) {
+    if (mixed) ratio_batched_impl<float, float>(L, P, t, nch, ratio, grad, lap);
+    else ratio_batched_impl<double, double>(L, P, t, nch, ratio, grad, lap);
+}
+
+void launch_accept_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const uint8_t* accept,
+                           const double* rnew) {
+    L.count();
+    if (mixed)
+        k_accept_batched<float, float><<<P.n_blk, kBlock, P.accept_smem, L.stream>>>(P.sys, P.blk, t, nch, accept, rnew);
+    else
+        k_accept_batched<double, double><<<P.n_blk, kBlock, P.accept_smem, L.stream>>>(P.sys, P.blk, t, nch, accept,
+                                                                                       rnew);
+}
+
+void launch_propose_batched(const Launch& L, const BatchPlan& P, int W_total, int t, const double* eta, double tau,
+                            double* rnew) {
+    L.count();
+    k_propose_batched<<<(W_total * 3 + 255) / 256, 256, 0, L.stream>>>(P.sys, P.wsys, W_total, t, eta, tau, rnew);
+}
+
+size_t accept_smem_bytes(int n) {
+    const int np = kBlock >= 2 * n ? kBlock / n : 1;
+    return (size_t)n * (3 + np) * 8;
+}
+
+int orbital_tile_points() { return kOrbTP; }
+int orbital_tile_orbitals() { return kOrbTJ; }
 
 }  // namespace msd
