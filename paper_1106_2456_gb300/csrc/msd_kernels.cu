@@ -411,9 +411,11 @@ __global__ void __launch_bounds__(kBlock) k_ci_contract_light(int n_exc, int n_e
     const int b = off[u], e = off[u + 1];
     if (e - b > heavy_len) return;  // handled by k_ci_contract_heavy
     const TT* tw = t_other + (long long)w * n_exc_other;
-    double acc = 0.0;
-    for (int q = b; q < e; ++q) acc = fma(__ldg(c + q), double(tw[__ldg(other + q)]), acc);
-    C[(long long)w * n_exc + u] = TT(acc);
+    // accumulated in the table's precision (at most heavy_len terms; the FP32 path stays off
+    // the slow FP64 pipe)
+    TT acc = TT(0);
+    for (int q = b; q < e; ++q) acc = fma(TT(__ldg(c + q)), tw[__ldg(other + q)], acc);
+    C[(long long)w * n_exc + u] = acc;
 }
 
 template <typename TT>
@@ -426,9 +428,10 @@ __global__ void __launch_bounds__(kBlock) k_ci_contract_heavy(int n_exc, int n_e
     const int u = heavy[blockIdx.x];
     const int w = blockIdx.y;
     const TT* tw = t_other + (long long)w * n_exc_other;
-    double v[1] = {0.0};
+    TT part = TT(0);  // per-thread partial in the table's precision, summed across threads in FP64
     for (int q = off[u] + threadIdx.x; q < off[u + 1]; q += blockDim.x)
-        v[0] = fma(__ldg(c + q), double(tw[__ldg(other + q)]), v[0]);
+        part = fma(TT(__ldg(c + q)), tw[__ldg(other + q)], part);
+    double v[1] = {double(part)};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) C[(long long)w * n_exc + u] = TT(v[0]);
 }
@@ -607,10 +610,9 @@ __device__ __forceinline__ void ratio_block(const RatioArgs& a, const int w, int
         xd[c] = v;
         xs[c] = TT(v);
     }
-    for (int idx = tid; idx < NC * n; idx += bd) {
-        const int al = idx / n, c = idx - al * n;
-        ph[idx] = phw[al * N + c];
-    }
+#pragma unroll
+    for (int al = 0; al < NC; ++al)
+        for (int c = tid; c < n; c += bd) ph[al * n + c] = phw[al * N + c];
     for (int q = tid; q < (m > 0 ? m : 1); q += bd) G1[q] = TT(0);
     for (int q = tid; q < NGW * (m > 0 ? m : 1); q += bd) Gw[q] = TT(0);
     __syncthreads();
