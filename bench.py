@@ -393,6 +393,72 @@ def run_batched(args):
     return 0
 
 
+def run_fig3(args):
+    """Table method against the canonical method (every determinant's own inverse updated by
+    Sherman-Morrison), both FP64 on the GPU: walker-moves/s of ratio + grad + lap + accept as the
+    number of determinants grows (the comparison of the paper's Fig. 3, on synthetic inputs)."""
+    import torch
+
+    from paper_1106_2456_gb300 import msd, workloads
+    import __graft_entry__
+
+    __graft_entry__.build()
+    msd.load_library()
+    W = args.walkers or 256
+    cases = []
+    for n, N, dets in ((5, 20, (100, 300, 1000, 3000)), (16, 48, (100, 1000, 3000))):
+        for nd in dets:
+            wl = workloads.custom_workload((n, n), (N, N), nd, workloads.uniform_orders(1, 4), W=W,
+                                           n_nuc=max(3, -(-N // 12)), seed=1000 + nd + n, K=n)
+            p = wl.problem
+            steps = 2 * p.n_tot
+            eta, u = wl.proposals(steps + 4)
+            eta = torch.tensor(eta, device="cuda")
+            u = torch.tensor(u, device="cuda")
+            row = {"n": n, "N": N, "n_det": nd, "strings": [p.n_exc(0), p.n_exc(1)]}
+            for method in ("fp64", "canonical"):
+                c = msd.MSD(p, W, method, refresh_K=wl.refresh_K)
+                c.set_positions(torch.tensor(wl.R0, device="cuda"))
+                rnew = torch.empty(W, 3, dtype=torch.float64, device="cuda")
+                r = torch.empty(W, dtype=torch.float64, device="cuda")
+                g = torch.empty(W, 3, dtype=torch.float64, device="cuda")
+                lp = torch.empty(W, dtype=torch.float64, device="cuda")
+                acc = torch.empty(W, dtype=torch.uint8, device="cuda")
+
+                def step(t):
+                    e = t % p.n_tot
+                    c.propose(e, eta[t], wl.tau, rnew)
+                    c.ratio_into(e, rnew, r, g, lp)
+                    c.metropolis(u[t], r, acc)
+                    c.accept(e, acc)
+
+                for t in range(4):
+                    step(t)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for t in range(4, 4 + steps):
+                    step(t)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                c.sync()
+                c.close()
+                row["table_ms" if method == "fp64" else "canonical_ms"] = ms
+            row["speedup"] = row["canonical_ms"] / row["table_ms"]
+            cases.append(row)
+    best = max(cases, key=lambda r: r["n_det"] * r["n"])
+    line = {"metric": "table vs canonical method, walker-moves/s (ratio+grad+lap+accept), FP64", "value":
+            W / (best["table_ms"] * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 4,
+            "ms_per_step": best["table_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fig3: n per spin 5 and 16, N = 4n or 3n, orders 1-4, {W} walkers, "
+                                   "refresh every n steps of a spin"},
+            "cases": cases}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -603,6 +669,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "fig3":
+        return run_fig3(args)
     return run_ours(args)
 
 

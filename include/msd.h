@@ -58,9 +58,14 @@ typedef enum {
 
 typedef enum {
     MSD_FP64 = 0,   /* every step in FP64 */
-    MSD_MIXED = 1   /* orbitals, table and excitation determinants in FP32; A_0^{-1},
+    MSD_MIXED = 1,  /* orbitals, table and excitation determinants in FP32; A_0^{-1},
                        its Sherman-Morrison update, the refresh LU, log|det| and the
                        final CI sums in FP64 */
+    MSD_CANONICAL = 2  /* FP64 without the table: every determinant keeps its own inverse,
+                       updated by Sherman-Morrison on accept (the method Section III improves
+                       on; for comparison).  msd_set_positions, msd_ratio, msd_accept,
+                       msd_propose, msd_metropolis, msd_get_state, msd_sync only; memory
+                       W x strings x n^2 doubles per spin. */
 } msd_precision;
 
 /*

@@ -81,6 +81,13 @@ struct msd_ctx {
     // staging for the host-buffer entry points
     double* d_io = nullptr;    // [W][8]
     uint8_t* d_acc = nullptr;  // [W]
+    // the canonical method (MSD_CANONICAL): per spin every string's inverse and det ratio
+    bool canon = false;
+    double* cn_D[2] = {nullptr, nullptr};    // [W][n_exc][n][n]
+    double* cn_t[2] = {nullptr, nullptr};    // [W][n_exc]
+    double* cn_ru[2] = {nullptr, nullptr};   // [W][n_exc] row ratios of the proposal
+    double* cn_Phi[2] = {nullptr, nullptr};  // [W][n][N] orbitals of the current positions
+    uint8_t* cn_used[2] = {nullptr, nullptr};
     // msd_backward: internal strings of every term, and workspace allocated on first use
     long long n_det = 0;
     int* term_iu = nullptr;    // [n_det] internal up string of term I
@@ -183,7 +190,8 @@ msd_status validate(const msd_problem* p) {
     if (!p) return fail(nullptr, MSD_ERR_ARG, "problem is NULL");
     if (p->n_walkers < 1) return fail(nullptr, MSD_ERR_ARG, "n_walkers must be >= 1");
     if (p->refresh_K < 1) return fail(nullptr, MSD_ERR_ARG, "refresh_K must be >= 1");
-    if (p->prec != MSD_FP64 && p->prec != MSD_MIXED) return fail(nullptr, MSD_ERR_ARG, "unknown precision");
+    if (p->prec != MSD_FP64 && p->prec != MSD_MIXED && p->prec != MSD_CANONICAL)
+        return fail(nullptr, MSD_ERR_ARG, "unknown precision");
     if (p->n_nuc < 1 || !p->nuc_xyz) return fail(nullptr, MSD_ERR_ARG, "need at least one nucleus");
     if (p->n_basis < 1 || !p->bas_center || !p->bas_lm || !p->bas_alpha)
         return fail(nullptr, MSD_ERR_ARG, "basis arrays missing");
@@ -513,7 +521,18 @@ msd_status set_positions(msd_ctx* c, State& st, const double* R_dev) {
 
 // Everything from scratch at the positions in st.R (Section III: inverse and determinants
 // "calculated from scratch").
+msd_status canon_refresh(msd_ctx* c, State& st, int s);
+msd_status canon_C(msd_ctx* c, State& st, int s, bool with_S);
+
 msd_status rebuild(msd_ctx* c, State& st) {
+    if (c->canon) {
+        TRY(canon_refresh(c, st, 0));
+        TRY(canon_refresh(c, st, 1));
+        st.C_valid[0] = st.C_valid[1] = false;
+        TRY(canon_C(c, st, 0, true));
+        st.ready = true;
+        return MSD_OK;
+    }
     TRY(refresh_spin(c, st, 0));
     TRY(refresh_spin(c, st, 1));
     st.C_valid[0] = st.C_valid[1] = false;
@@ -521,6 +540,34 @@ msd_status rebuild(msd_ctx* c, State& st) {
     TRY(recompute_S(c, st, 0));
     st.ready = true;
     return MSD_OK;
+}
+
+// The canonical method: every string's inverse and det ratio of spin s from scratch at the
+// positions in st.R (orbitals of all the spin's electrons, the reference inverse for det A_0).
+msd_status canon_refresh(msd_ctx* c, State& st, int s) {
+    const SpinConst& S = c->sp[s];
+    launch_orbitals(c->L(), false, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas, c->blm, c->nb,
+                    S.B, S.N, c->cn_Phi[s]);
+    launch_inverse(c->L(), false, c->W, S.n, S.N, c->cn_Phi[s], st.Ainv[s], st.logdet[s], st.sgn[s]);
+    launch_canon_build(c->L(), c->W, S.n, S.N, S.m, S.g, c->cn_Phi[s], c->cn_used[s], st.logdet[s], st.sgn[s],
+                       c->cn_D[s], c->cn_t[s]);
+    st.since_refresh[s] = 0;
+    st.C_valid[1 - s] = false;
+    return check_launch(c, "canonical refresh");
+}
+
+// C_s from the other spin's det ratios, then S = sum_u C_s[u] t_s[u].
+msd_status canon_C(msd_ctx* c, State& st, int s, bool with_S) {
+    const SpinConst& S = c->sp[s];
+    const SpinConst& O = c->sp[1 - s];
+    if (!st.C_valid[s]) {
+        launch_ci_contract(c->L(), false, c->W, S.g.n_exc, O.g.n_exc, S.t_off, S.t_other, S.t_c, c->cn_t[1 - s], st.C[s]);
+        launch_ci_contract_heavy(c->L(), false, c->W, S.g.n_exc, O.g.n_exc, S.n_heavy, S.heavy, S.t_off, S.t_other,
+                                 S.t_c, c->cn_t[1 - s], st.C[s]);
+        st.C_valid[s] = true;
+    }
+    if (with_S) launch_ci_dot(c->L(), false, c->W, S.g.n_exc, st.C[s], c->cn_t[s], st.S);
+    return check_launch(c, "canonical CI sums");
 }
 
 int spin_of(const msd_ctx* c, int e) { return e < c->sp[0].n ? 0 : 1; }
@@ -808,6 +855,7 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     c->nb = p->n_basis;
     c->K = p->refresh_K;
     c->mixed = p->prec == MSD_MIXED;
+    c->canon = p->prec == MSD_CANONICAL;
     c->tb = c->mixed ? 4 : 8;
     c->stream = static_cast<cudaStream_t>(p->cuda_stream);
     auto bail = [&](msd_status s) {
@@ -860,6 +908,18 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     if ((st = dalloc(c, &c->d_status, 1)) != MSD_OK) return bail(st);
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(c, MSD_ERR_CUDA, "memset"));
     if ((st = alloc_state(c, c->st)) != MSD_OK) return bail(st);
+    if (c->canon) {
+        for (int s = 0; s < 2; ++s) {
+            const SpinConst& S = c->sp[s];
+            std::vector<uint8_t> used(S.g.n_exc);
+            for (int j = 0; j < S.g.n_exc; ++j) used[j] = S.user_of[j] >= 0;
+            if ((st = upload(c, &c->cn_used[s], used.data(), used.size())) != MSD_OK) return bail(st);
+            if ((st = dalloc(c, &c->cn_D[s], (size_t)W * S.g.n_exc * S.n * S.n)) != MSD_OK) return bail(st);
+            if ((st = dalloc(c, &c->cn_t[s], (size_t)W * S.g.n_exc)) != MSD_OK) return bail(st);
+            if ((st = dalloc(c, &c->cn_ru[s], (size_t)W * S.g.n_exc)) != MSD_OK) return bail(st);
+            if ((st = dalloc(c, &c->cn_Phi[s], (size_t)W * S.n * S.N)) != MSD_OK) return bail(st);
+        }
+    }
     {
         c->n_det = p->n_det;
         std::vector<int> iu(p->n_det), id(p->n_det);
@@ -924,6 +984,32 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
     if ((grad_dev == nullptr) != (lap_dev == nullptr))
         return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    if (c->canon) {
+        State& st = c->st;
+        const int s = spin_of(c, elec);
+        const SpinConst& S = c->sp[s];
+        if (st.since_refresh[s] >= c->K) {
+            TRY(canon_refresh(c, st, s));
+            TRY(canon_C(c, st, s, true));
+        } else {
+            TRY(canon_C(c, st, s, false));
+        }
+        st.since_refresh[s]++;
+        const int nch = grad_dev ? NCH : 1;
+        cudaError_t e = cudaMemcpyAsync(c->rnew, rnew_dev, sizeof(double) * c->W * 3, cudaMemcpyDeviceToDevice,
+                                        c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
+        launch_orbitals(c->L(), false, nch, c->W, 1, c->rnew, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, c->phi_new);
+        launch_canon_ratio(c->L_sweep(), c->W, S.n, S.N, S.m, elec - S.off, nch, S.g, c->cn_used[s],
+                           static_cast<const double*>(c->phi_new), c->cn_D[s], c->cn_t[s],
+                           static_cast<const double*>(st.C[s]), st.S, c->cn_ru[s], ratio_dev, grad_dev, lap_dev,
+                           c->num, c->rho);
+        TRY(check_launch(c, "canonical ratio"));
+        c->prop_elec = elec;
+        c->prop_nch = nch;
+        c->prop_valid = true;
+        return MSD_OK;
+    }
     State& st = c->st;
     const int s = spin_of(c, elec);
     const SpinConst& S = c->sp[s];
@@ -958,6 +1044,17 @@ msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
     if (!c || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     if (!c->prop_valid || c->prop_elec != elec)
         return fail(c, MSD_ERR_STATE, "msd_accept(%d) without a matching msd_ratio proposal", elec);
+    if (c->canon) {
+        State& st = c->st;
+        const int s = spin_of(c, elec);
+        const SpinConst& S = c->sp[s];
+        launch_canon_accept(c->L(), c->W, S.n, S.N, S.m, elec - S.off, elec, c->n_tot, S.g, c->cn_used[s], accept_dev,
+                            static_cast<const double*>(c->phi_new), c->prop_nch, c->cn_Phi[s], c->cn_D[s], c->cn_t[s],
+                            c->cn_ru[s], c->rnew, st.R, c->rho, c->num, st.logdet[s], st.sgn[s], st.S);
+        st.C_valid[1 - s] = false;
+        c->prop_valid = false;
+        return check_launch(c, "canonical accept");
+    }
     State& st = c->st;
     const int s = spin_of(c, elec);
     const SpinConst& S = c->sp[s];
@@ -973,6 +1070,7 @@ msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
 }
 
 msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c) && grad_dev && lap_dev && elec >= -1)
         return batch_each(c, [&](int s, msd_ctx* sc) {
             // one electron: [W_s][3] per system; all electrons: [W_s][n_tot_s][3] per system
@@ -991,6 +1089,7 @@ msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_
 
 msd_status msd_eval_batch(msd_ctx* c, const double* R_dev, double* logabs_dev, double* sign_dev, double* grad_dev,
                           double* lap_dev) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c) && R_dev && logabs_dev && sign_dev)
         return batch_each(c, [&](int s, msd_ctx* sc) {
             const long long w = c->w_off[s], r = c->r_off[s];
@@ -1254,6 +1353,7 @@ void msd_destroy(msd_ctx* c) {
 
 msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
                              double* lap_dev) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c))  // its scratch is one array per device: systems on concurrent streams would share it
         return fail(c, MSD_ERR_ARG, "msd_ratio_noalloc takes a single-system context");
     if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
@@ -1287,6 +1387,7 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
 }
 
 msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, double* dB_dev) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c) && gbar_dev && dci_dev && dB_dev)
         return batch_each(c, [&](int q, msd_ctx* sc) {
             return msd_backward(sc, gbar_dev + c->w_off[q], dci_dev + c->det_off[q], dB_dev + c->b_off[q]);
@@ -1332,6 +1433,7 @@ msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, dou
 }
 
 msd_status msd_set_params(msd_ctx* c, const double* ci_host, const double* B_up_host, const double* B_dn_host) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c)) {
         for (size_t q = 0; q < c->sub.size(); ++q) {
             const msd_ctx* sc = c->sub[q];

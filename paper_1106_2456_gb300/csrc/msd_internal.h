@@ -172,6 +172,19 @@ size_t accept_smem_bytes(int n);
 int orbital_tile_points();
 int orbital_tile_orbitals();
 
+// The canonical method (msd_kernels.cu): D[w][j] = A_j^{-1} ([c][r]) and t[w][j] = det A_j / det A_0
+// of every string j, the row-replacement ratios ru[w][j] of a proposal, their update on accept.
+void launch_canon_build(const Launch& L, int W, int n, int N, int m, const ExcDev& g, const double* Phi,
+                        const uint8_t* used, const double* ld0, const double* sg0, double* D, double* t);
+void launch_canon_ratio(const Launch& L, int W, int n, int N, int m, int row, int nch, const ExcDev& g,
+                        const uint8_t* used, const double* phi, const double* D, const double* t, const double* C,
+                        const double* S, double* ru, double* ratio, double* grad, double* lap, double* num,
+                        double* rho);
+void launch_canon_accept(const Launch& L, int W, int n, int N, int m, int row, int elec, int n_tot, const ExcDev& g,
+                         const uint8_t* used, const uint8_t* accept, const double* phi_new, int nch, double* Phi,
+                         double* D, double* t, const double* ru, const double* rnew, double* R, const double* rho,
+                         const double* num, double* logdet, double* sgn, double* S);
+
 // Adjoint of log|Psi| (msd_backward.cu).  dci[I] += sum_w gbar[w] t0[w][iu[I]] t1[w][id[I]] / S[w].
 void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* iu, const int* id, const double* gbar,
                 const double* S, const void* t0, int ld0, const void* t1, int ld1, double* dci);

@@ -189,9 +189,10 @@ __global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* 
 // A7: from-scratch inverse of A_0 (Gauss-Jordan with partial pivoting, FP64, one block per walker)
 // ------------------------------------------------------------------------------------------
 template <typename TO>
-__global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __restrict__ Phi,
-                                                    double* __restrict__ Ainv, double* __restrict__ logdet,
-                                                    double* __restrict__ sgn, int* __restrict__ status) {
+__device__ __forceinline__ void inverse_block(int n, int N, const TO* __restrict__ src, const int* cols,
+                                              double* __restrict__ dst, double* __restrict__ logdet_out,
+                                              double* __restrict__ sgn_out, int* __restrict__ status) {
+    // A[r][c] = src[r * N + col(c)], col(c) = cols ? cols[c] : c (a shared-memory map)
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = n + 1;
     double* a = reinterpret_cast<double*>(smem);  // [n][ld]
@@ -199,16 +200,15 @@ __global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __re
     int* piv = reinterpret_cast<int*>(f + n);     // [n]
     __shared__ int s_p, s_bad;
     __shared__ double s_logdet, s_sign, s_amax[32];
-    const int w = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+    const int tid = threadIdx.x, bd = blockDim.x;
     const int tx = tid & 31, ty = tid >> 5, ny = bd >> 5;
-    const TO* src = Phi + (long long)w * n * N;
     // Eliminate on B = A_0^T: row operations on B give X with X B = I up to rounding, so
     // A_0 X^T = I has a small residual -- the identity phi_occ(r_i)^T A_0^{-1} = e_i^T that the
     // Sherman-Morrison row update and the table update rely on.
     double amax = 0.0;
     for (int c = ty; c < n; c += ny)
         for (int r = tx; r < n; r += 32) {
-            const double v = double(src[(long long)r * N + c]);
+            const double v = double(src[(long long)r * N + (cols ? cols[c] : c)]);
             a[c * ld + r] = v;  // a = A_0^T
             amax = fmax(amax, fabs(v));
         }
@@ -286,13 +286,201 @@ __global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __re
         __syncthreads();
     }
     // a now holds (A_0^T)^{-1} = (A_0^{-1})^T; store A_0^{-1}[c][r] = a[r][c]
-    double* dst = Ainv + (long long)w * n * n;
     for (int c = ty; c < n; c += ny)
         for (int r = tx; r < n; r += 32) dst[c * n + r] = a[r * ld + c];
     if (tid == 0) {
-        logdet[w] = s_bad ? -INFINITY : s_logdet;
-        sgn[w] = s_bad ? 0.0 : s_sign;
-        if (s_bad) atomicOr(status, ST_SINGULAR);
+        *logdet_out = s_bad ? -INFINITY : s_logdet;
+        *sgn_out = s_bad ? 0.0 : s_sign;
+        if (s_bad && status) atomicOr(status, ST_SINGULAR);
+    }
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __restrict__ Phi,
+                                                    double* __restrict__ Ainv, double* __restrict__ logdet,
+                                                    double* __restrict__ sgn, int* __restrict__ status) {
+    const int w = blockIdx.x;
+    inverse_block<TO>(n, N, Phi + (long long)w * n * N, nullptr, Ainv + (long long)w * n * n, logdet + w, sgn + w,
+                      status);
+}
+
+// ------------------------------------------------------------------------------------------
+// The canonical method (Section III's point of comparison): every determinant A_u keeps its
+// own inverse, updated by Sherman-Morrison after each accepted move.  FP64.
+// ------------------------------------------------------------------------------------------
+// Column map of string j of one spin: col(c) = c, except hole h_q -> n + p_q.
+__device__ __forceinline__ bool string_columns(const ExcDev& g, int n, int m, int j, int* cols) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) cols[c] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int k = 0;
+        while (k <= g.kmax && j >= g.goff[k + 1]) ++k;
+        if (k == 1 && g.dense1) {
+            const int q = j - g.goff[1];
+            cols[q / m] = n + q % m;
+        } else if (k >= 1) {
+            const uint8_t* r = g.rec + g.roff[k] + (long long)(j - g.goff[k]) * rec_bytes(k);
+            if (r[0] == kEmptyRecord) cols[0] = -1;
+            else
+                for (int q = 0; q < k; ++q) cols[r[q]] = n + r[k + q];
+        }
+    }
+    __syncthreads();
+    return cols[0] >= 0;
+}
+
+// Inverse and det A_u / det A_0 of every string (grid: strings x walkers).
+__global__ void __launch_bounds__(kBlock) k_canon_build(int n, int N, int m, ExcDev g, const double* __restrict__ Phi,
+                                                        const uint8_t* __restrict__ used, const double* __restrict__ ld0,
+                                                        const double* __restrict__ sg0, double* __restrict__ D,
+                                                        double* __restrict__ t, int* __restrict__ status) {
+    __shared__ int cols[MSD_MAX_ORB];
+    __shared__ double s_ld, s_sg;
+    const int j = blockIdx.x, w = blockIdx.y;
+    double* tw = t + (long long)w * g.n_exc + j;
+    if (!used[j] || !string_columns(g, n, m, j, cols)) {
+        if (threadIdx.x == 0) *tw = 0.0;
+        return;
+    }
+    inverse_block<double>(n, N, Phi + (long long)w * n * N, cols, D + ((long long)w * g.n_exc + j) * n * n, &s_ld, &s_sg,
+                          nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) *tw = s_sg * sg0[w] * exp(s_ld - ld0[w]);
+}
+
+// Ratio, gradient and laplacian of a move of row `row`: every string's row-i replacement
+// ratio d^a_u = sum_c d^a phi_col(c)(r') D_u[c][row], combined as sum_u C_u t_u d^a_u.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_canon_ratio(int n, int N, int m, int row, ExcDev g,
+                                                        const uint8_t* __restrict__ used, const double* __restrict__ phi,
+                                                        const double* __restrict__ D, const double* __restrict__ t,
+                                                        const double* __restrict__ C, const double* __restrict__ S,
+                                                        double* __restrict__ ru, double* ratio, double* grad,
+                                                        double* lap, double* num_out, double* rho_out,
+                                                        int* __restrict__ status) {
+    __shared__ double red[32 * NC];
+    const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* ph = phi + (long long)w * NC * N;
+    double acc[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) acc[a] = 0.0;
+    for (int j = warp; j < g.n_exc; j += nw) {
+        const double cj = C[(long long)w * g.n_exc + j];
+        if (!used[j]) continue;
+        // this lane's columns c = lane, lane + 32, ...: col(c) from the string's holes
+        int k = 0;
+        while (k <= g.kmax && j >= g.goff[k + 1]) ++k;
+        int hq[MSD_MAX_ORDER], pq[MSD_MAX_ORDER], kk = 0;
+        if (k == 1 && g.dense1) {
+            const int q = j - g.goff[1];
+            hq[0] = q / m;
+            pq[0] = q % m;
+            kk = 1;
+        } else if (k >= 1) {
+            const uint8_t* r = g.rec + g.roff[k] + (long long)(j - g.goff[k]) * rec_bytes(k);
+            if (r[0] == kEmptyRecord) continue;
+            for (int q = 0; q < k; ++q) { hq[q] = r[q]; pq[q] = r[k + q]; }
+            kk = k;
+        }
+        const double* Dj = D + ((long long)w * g.n_exc + j) * n * n;
+        double v[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) v[a] = 0.0;
+        for (int c = lane; c < n; c += 32) {
+            int col = c;
+            for (int q = 0; q < kk; ++q)
+                if (hq[q] == c) col = n + pq[q];
+            const double dci = Dj[(long long)c * n + row];
+#pragma unroll
+            for (int a = 0; a < NC; ++a) v[a] = fma(ph[a * N + col], dci, v[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a) v[a] = warp_sum(v[a]);
+        if (lane == 0) {
+            ru[(long long)w * g.n_exc + j] = v[0];
+            const double wt = cj * t[(long long)w * g.n_exc + j];
+#pragma unroll
+            for (int a = 0; a < NC; ++a) acc[a] = fma(wt, v[a], acc[a]);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < NC; ++a) red[warp * NC + a] = acc[a];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double num[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            double s = 0.0;
+            for (int q = 0; q < nw; ++q) s += red[q * NC + a];
+            num[a] = s;
+        }
+        const double r = num[0] / S[w];
+        ratio[w] = r;
+        if constexpr (NC == 5) {
+            for (int d = 0; d < 3; ++d) grad[(long long)w * 3 + d] = num[1 + d] / num[0];
+            lap[w] = num[4] / num[0];
+        }
+        for (int a = 0; a < NCH; ++a) num_out[(long long)w * NCH + a] = a < NC ? num[a] : 0.0;
+        rho_out[w] = ru[(long long)w * g.n_exc];  // the reference string's row ratio
+        if (!isfinite(r)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// Sherman-Morrison update of every string's inverse of an accepted walker (grid: strings x
+// walkers); t_u <- t_u ratio_u / ratio_0.  The row of the old orbitals comes from Phi.
+__global__ void __launch_bounds__(kBlock) k_canon_accept(int n, int N, int m, int row, ExcDev g,
+                                                         const uint8_t* __restrict__ used,
+                                                         const uint8_t* __restrict__ accept,
+                                                         const double* __restrict__ phi_new, int nch,
+                                                         const double* __restrict__ Phi, double* __restrict__ D,
+                                                         double* __restrict__ t, const double* __restrict__ ru) {
+    __shared__ int cols[MSD_MAX_ORB];
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* delta = reinterpret_cast<double*>(smem);  // [n]
+    double* uu = delta + n;                           // [n] delta^T D
+    double* di = uu + n;                              // [n] column `row` of D
+    const int j = blockIdx.x, w = blockIdx.y;
+    if (!accept[w] || !used[j] || !string_columns(g, n, m, j, cols)) return;
+    double* Dj = D + ((long long)w * g.n_exc + j) * n * n;
+    const double* pn = phi_new + (long long)w * nch * N;
+    const double* po = Phi + ((long long)w * n + row) * N;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        delta[c] = pn[cols[c]] - po[cols[c]];
+        di[c] = Dj[(long long)c * n + row];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double a = 0.0;
+        for (int c = 0; c < n; ++c) a = fma(delta[c], Dj[(long long)c * n + r], a);
+        uu[r] = a;
+    }
+    __syncthreads();
+    const double rj = ru[(long long)w * g.n_exc + j];  // = 1 + delta^T D e_row
+    const double inv = 1.0 / rj;
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) {
+        const int c = int(q / n), r = int(q - (long long)c * n);
+        Dj[q] = fma(-di[c] * inv, uu[r], Dj[q]);
+    }
+    if (threadIdx.x == 0) t[(long long)w * g.n_exc + j] *= rj / ru[(long long)w * g.n_exc];
+}
+
+// Per accepted walker: the moved row of Phi, the position, the reference determinant and S.
+__global__ void k_canon_commit(int W, int n, int N, int row, int elec, int n_tot, int nch,
+                               const uint8_t* __restrict__ accept, const double* __restrict__ phi_new,
+                               double* __restrict__ Phi, const double* __restrict__ rnew, double* __restrict__ R,
+                               const double* __restrict__ rho, const double* __restrict__ num,
+                               double* __restrict__ logdet, double* __restrict__ sgn, double* __restrict__ S) {
+    const int w = blockIdx.x;
+    if (!accept[w]) return;
+    for (int jj = threadIdx.x; jj < N; jj += blockDim.x)
+        Phi[((long long)w * n + row) * N + jj] = phi_new[(long long)w * nch * N + jj];
+    if (threadIdx.x == 0) {
+        const double r0 = rho[w];
+        logdet[w] += log(fabs(r0));
+        if (r0 < 0.0) sgn[w] = -sgn[w];
+        S[w] = num[(long long)w * NCH] / r0;
+        for (int d = 0; d < 3; ++d) R[((long long)w * n_tot + elec) * 3 + d] = rnew[w * 3 + d];
     }
 }
 
@@ -1220,5 +1408,40 @@ size_t accept_smem_bytes(int n) {
 
 int orbital_tile_points() { return kOrbTP; }
 int orbital_tile_orbitals() { return kOrbTJ; }
+
+void launch_canon_build(const Launch& L, int W, int n, int N, int m, const ExcDev& g, const double* Phi,
+                        const uint8_t* used, const double* ld0, const double* sg0, double* D, double* t) {
+    const size_t sm = (size_t)n * (n + 1) * 8 + (size_t)n * 12 + 16;
+    set_smem(k_canon_build, sm);
+    L.count();
+    k_canon_build<<<dim3(g.n_exc, W), kBlock, sm, L.stream>>>(n, N, m, g, Phi, used, ld0, sg0, D, t, L.status);
+}
+
+void launch_canon_ratio(const Launch& L, int W, int n, int N, int m, int row, int nch, const ExcDev& g,
+                        const uint8_t* used, const double* phi, const double* D, const double* t, const double* C,
+                        const double* S, double* ru, double* ratio, double* grad, double* lap, double* num,
+                        double* rho) {
+    if (L.t0) cudaEventRecord(L.t0, L.stream);
+    L.count();
+    if (nch == 5)
+        k_canon_ratio<5><<<W, kBlock, 0, L.stream>>>(n, N, m, row, g, used, phi, D, t, C, S, ru, ratio, grad, lap, num,
+                                                     rho, L.status);
+    else
+        k_canon_ratio<1><<<W, kBlock, 0, L.stream>>>(n, N, m, row, g, used, phi, D, t, C, S, ru, ratio, grad, lap, num,
+                                                     rho, L.status);
+    if (L.t1) cudaEventRecord(L.t1, L.stream);
+}
+
+void launch_canon_accept(const Launch& L, int W, int n, int N, int m, int row, int elec, int n_tot, const ExcDev& g,
+                         const uint8_t* used, const uint8_t* accept, const double* phi_new, int nch, double* Phi,
+                         double* D, double* t, const double* ru, const double* rnew, double* R, const double* rho,
+                         const double* num, double* logdet, double* sgn, double* S) {
+    L.count();
+    k_canon_accept<<<dim3(g.n_exc, W), kBlock, (size_t)3 * n * 8, L.stream>>>(n, N, m, row, g, used, accept, phi_new,
+                                                                              nch, Phi, D, t, ru);
+    L.count();
+    k_canon_commit<<<W, 128, 0, L.stream>>>(W, n, N, row, elec, n_tot, nch, accept, phi_new, Phi, rnew, R, rho, num,
+                                            logdet, sgn, S);
+}
 
 }  // namespace msd

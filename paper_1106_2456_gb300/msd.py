@@ -18,7 +18,7 @@ import torch
 
 from .build import INCLUDE, library_path
 
-MSD_FP64, MSD_MIXED = 0, 1
+MSD_FP64, MSD_MIXED, MSD_CANONICAL = 0, 1, 2
 _STATUS = {0: "MSD_OK", 1: "MSD_ERR_ARG", 2: "MSD_ERR_CUDA", 3: "MSD_ERR_OOM", 4: "MSD_ERR_SINGULAR",
            5: "MSD_ERR_TIMEOUT", 6: "MSD_ERR_STATE"}
 NCH = 5
@@ -156,7 +156,7 @@ def problem_struct(problem, n_walkers: int, precision: str, refresh_K: int = 1 <
     s.det_dn = arr(problem.det_dn, np.int32)
     s.ci = arr(problem.ci, np.float64)
     s.n_walkers = int(n_walkers)
-    s.prec = MSD_MIXED if precision == "mixed" else MSD_FP64
+    s.prec = {"fp64": MSD_FP64, "mixed": MSD_MIXED, "canonical": MSD_CANONICAL}[precision]
     s.refresh_K = int(min(refresh_K, 2 ** 31 - 1))
     s.cuda_stream = stream_handle
     return s, keep
@@ -185,8 +185,8 @@ class MSD:
         self.W = int(n_walkers)
         self.n_tot = problem.n_tot
         self.mixed = precision == "mixed"
-        if precision not in ("fp64", "mixed"):
-            raise ValueError("precision must be 'fp64' or 'mixed'")
+        if precision not in ("fp64", "mixed", "canonical"):
+            raise ValueError("precision must be 'fp64', 'mixed' or 'canonical' (FP64, per-determinant inverses)")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         s, self._keep = problem_struct(problem, self.W, precision, refresh_K, self.stream.cuda_stream)
         ctx = ctypes.c_void_p()

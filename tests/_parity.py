@@ -47,7 +47,7 @@ def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = No
     `check` (default: all) with the oracle after every step.  Returns, per result kind and
     per step, the worst relative error and the worst ratio of error to the tolerance of the
     precision at that walker's conditioning (<= 1 passes)."""
-    tol_fn = tol_fp64 if precision == "fp64" else tol_mixed
+    tol_fn = tol_mixed if precision == "mixed" else tol_fp64
     p = wl.problem
     W = wl.n_walkers
     idx = np.arange(W) if check is None else np.asarray(check)
