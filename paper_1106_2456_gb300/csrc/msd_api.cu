@@ -88,6 +88,10 @@ struct msd_ctx {
     double* cn_ru[2] = {nullptr, nullptr};   // [W][n_exc] row ratios of the proposal
     double* cn_Phi[2] = {nullptr, nullptr};  // [W][n][N] orbitals of the current positions
     uint8_t* cn_used[2] = {nullptr, nullptr};
+    // all-electron gradient/laplacian workspace (allocated on first use)
+    double* ga_G = nullptr;    // [W][n_max][m_max]
+    double* ga_U = nullptr;    // [W][n_max][n_max]
+    void* ga_phid = nullptr;   // [W n_max][5][N_max]
     // msd_backward: internal strings of every term, and workspace allocated on first use
     long long n_det = 0;
     int* term_iu = nullptr;    // [n_det] internal up string of term I
@@ -1082,8 +1086,35 @@ msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_
     if (elec < -1 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
     if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
     if (elec >= 0) return grad_lap_one(c, c->st, elec, grad_dev, 3, lap_dev, 1);
-    for (int e = 0; e < c->n_tot; ++e)
-        TRY(grad_lap_one(c, c->st, e, grad_dev + 3 * e, 3LL * c->n_tot, lap_dev + e, c->n_tot));
+    // every electron at once: the cofactor scatter Tbar of each spin gives the G of a move of
+    // any electron i as (A_0^{-T} Tbar)[i], so one sweep per spin replaces n sweeps
+    {
+        State& st = c->st;
+        const size_t W = c->W;
+        const int nmax = std::max(c->sp[0].n, c->sp[1].n);
+        const int Nmax = std::max(c->sp[0].N, c->sp[1].N);
+        const int mmax = std::max(1, std::max(c->sp[0].m, c->sp[1].m));
+        if (!c->bw_M) TRY(dalloc(c, &c->bw_M, W * nmax * Nmax));
+        if (!c->ga_G) TRY(dalloc(c, &c->ga_G, W * nmax * mmax));
+        if (!c->ga_U) TRY(dalloc(c, &c->ga_U, W * nmax * nmax));
+        if (!c->ga_phid) TRY(valloc(c, &c->ga_phid, W * nmax * NCH * Nmax * c->tb));
+        for (int s = 0; s < 2; ++s) {
+            const SpinConst& S = c->sp[s];
+            if (tbar_smem_bytes(c->mixed, S.n, S.m) > 220 * 1024) {
+                // table and its adjoint exceed shared memory: one sweep per electron instead
+                for (int e = S.off; e < S.off + S.n; ++e)
+                    TRY(grad_lap_one(c, st, e, grad_dev + 3 * e, 3LL * c->n_tot, lap_dev + e, c->n_tot));
+                continue;
+            }
+            TRY(ensure_C(c, st, s));
+            launch_tbar(c->L(), c->mixed, c->W, S.n, S.m, S.N, S.g, st.T[s], st.C[s], st.S, c->bw_M);
+            launch_orbitals(c->L(), c->mixed, NCH, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas,
+                            c->blm, c->nb, S.B, S.N, c->ga_phid);
+            launch_all_gradlap(c->L(), c->mixed, c->W, S.n, S.m, S.N, c->n_tot, S.off, st.Ainv[s], st.T[s], c->bw_M,
+                               c->ga_phid, c->ga_G, c->ga_U, grad_dev, lap_dev);
+            TRY(check_launch(c, "all-electron gradient"));
+        }
+    }
     return MSD_OK;
 }
 

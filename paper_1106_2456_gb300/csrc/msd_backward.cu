@@ -211,6 +211,55 @@ __global__ void __launch_bounds__(kBB) k_dB(int P, int nb, int N, int pchunk, co
     }
 }
 
+// All-electron gradient and laplacian at the current positions (one spin), from Tbar:
+//   d^a Psi / Psi for electron i = s^a(i) + sum_p y^a_i[p] G'[i][p],
+//   s^a(i) = d^a phi_occ(r_i) . A_0^{-1}[:, i],  y^a_i = d^a phi_virt(r_i) - T^T d^a phi_occ(r_i),
+//   G'[i][p] = sum_h A_0^{-1}[h][i] Tbar[h][p]  (the G of a move of electron i, divided by S).
+// One block per walker; G' and U = T G'^T in global scratch.
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBB) k_all_gradlap(int n, int m, int N, int n_tot, int e_off,
+                                                    const double* __restrict__ Ainv, const TT* __restrict__ T,
+                                                    const double* __restrict__ M, const TO* __restrict__ phid,
+                                                    double* __restrict__ Gp, double* __restrict__ U,
+                                                    double* __restrict__ grad, double* __restrict__ lap) {
+    const int w = blockIdx.x;
+    const double* Aw = Ainv + (long long)w * n * n;
+    const TT* Tw = T + (long long)w * n * m;
+    const double* Mw = M + (long long)w * n * N;  // Tbar[h][p] at Mw[h * N + n + p]
+    double* Gw = Gp + (long long)w * n * m;
+    double* Uw = U + (long long)w * n * n;
+    for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
+        const int i = idx / m, p = idx - i * m;
+        double acc = 0.0;
+        for (int h = 0; h < n; ++h) acc = fma(Aw[(long long)h * n + i], Mw[(long long)h * N + n + p], acc);
+        Gw[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c = idx / n, i = idx - c * n;
+        double acc = 0.0;
+        for (int p = 0; p < m; ++p) acc = fma(double(Tw[(long long)c * m + p]), Gw[(long long)i * m + p], acc);
+        Uw[idx] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const TO* ph = phid + ((long long)w * n + i) * 5 * N;
+        double num[5];
+#pragma unroll
+        for (int a = 1; a < 5; ++a) {
+            const TO* pa = ph + a * N;
+            double v = 0.0;
+            for (int c = 0; c < n; ++c)
+                v = fma(double(pa[c]), Aw[(long long)c * n + i] - Uw[(long long)c * n + i], v);
+            for (int p = 0; p < m; ++p) v = fma(double(pa[n + p]), Gw[(long long)i * m + p], v);
+            num[a] = v;
+        }
+        const long long e = (long long)w * n_tot + e_off + i;
+        for (int d = 0; d < 3; ++d) grad[e * 3 + d] = num[1 + d];
+        lap[e] = num[4];
+    }
+}
+
 }  // namespace
 
 void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* iu, const int* id, const double* gbar,
@@ -272,6 +321,35 @@ void launch_dB(const Launch& L, int P, int nb, int N, const double* chi, const d
     dim3 grid((nb + 31) / 32, (N + 31) / 32, (P + pchunk - 1) / pchunk);
     L.count();
     k_dB<<<grid, kBB, 0, L.stream>>>(P, nb, N, pchunk, chi, Phib, dB);
+}
+
+void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T, const void* C,
+                 const double* S, double* M) {
+    const size_t sm = tbar_smem_bytes(mixed, n, m);
+    if (m <= 0) return;
+    if (mixed) {
+        cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        L.count();
+        k_tbar<float><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T), static_cast<const float*>(C),
+                                                S, M);
+    } else {
+        cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        L.count();
+        k_tbar<double><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+                                                 static_cast<const double*>(C), S, M);
+    }
+}
+
+void launch_all_gradlap(const Launch& L, bool mixed, int W, int n, int m, int N, int n_tot, int e_off,
+                        const double* Ainv, const void* T, const double* M, const void* phid, double* Gp, double* U,
+                        double* grad, double* lap) {
+    L.count();
+    if (mixed)
+        k_all_gradlap<float, float><<<W, kBB, 0, L.stream>>>(n, m, N, n_tot, e_off, Ainv, static_cast<const float*>(T), M,
+                                                           static_cast<const float*>(phid), Gp, U, grad, lap);
+    else
+        k_all_gradlap<double, double><<<W, kBB, 0, L.stream>>>(n, m, N, n_tot, e_off, Ainv, static_cast<const double*>(T),
+                                                             M, static_cast<const double*>(phid), Gp, U, grad, lap);
 }
 
 }  // namespace msd

@@ -192,6 +192,14 @@ void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* 
 size_t tbar_smem_bytes(bool mixed, int n, int m);
 void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T,
                    const void* C, const double* S, const double* Ainv, const double* gbar, double* M);
+// Tbar = (1/S) sum_u C_u cof(T_u) into columns n..N-1 of M (n x N, FP64).
+void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T, const void* C,
+                 const double* S, double* M);
+// grad [W][n_tot][3] and lap [W][n_tot] of the spin's electrons e_off .. e_off + n - 1 from Tbar
+// (in M) and the orbitals with derivatives at every electron, phid [W n][5][N].
+void launch_all_gradlap(const Launch& L, bool mixed, int W, int n, int m, int N, int n_tot, int e_off,
+                        const double* Ainv, const void* T, const double* M, const void* phid, double* Gp, double* U,
+                        double* grad, double* lap);
 // chi[p][mu] (values, FP64) at P points laid out as for launch_orbitals.
 void launch_chi(const Launch& L, int P, int ppw, const double* pos, long long wstride, int p_off, const double4* bas,
                 const int8_t* blm, int nb, double* chi);
