@@ -27,8 +27,8 @@
  *   - Arrays are C-contiguous (row-major) with the stated shapes; W = n_walkers.
  *     Walker positions are [W][n_up + n_dn][3] doubles in bohr, up electrons first.
  *   - No call allocates after msd_init, except on first use msd_eval_batch (it creates a
- *     second walker state so that the main one is left untouched) and msd_backward (its
- *     workspace).
+ *     second walker state so that the main one is left untouched), msd_backward and
+ *     msd_grad_lap with elec = -1 (their workspaces).
  *   - Device-side numerical faults (a zero or non-finite pivot, a non-finite ratio)
  *     set a status word that msd_sync reports; host-side argument errors return
  *     MSD_ERR_ARG and leave the context unchanged.  msd_last_error explains the
@@ -156,7 +156,9 @@ msd_status msd_ratio(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double*
 msd_status msd_accept(msd_ctx* ctx, int32_t elec, const uint8_t* accept_dev);
 
 /* grad_elec Psi / Psi [W][3] and lap_elec Psi / Psi [W] at the current positions.
- * elec = -1 evaluates every electron: grad_dev [W][n_tot][3], lap_dev [W][n_tot]. */
+ * elec = -1 evaluates every electron: grad_dev [W][n_tot][3], lap_dev [W][n_tot], from one
+ * cofactor scatter per spin (the G of a move of electron i is A_0^{-T} Tbar, row i) instead
+ * of one sweep per electron. */
 msd_status msd_grad_lap(msd_ctx* ctx, int32_t elec, double* grad_dev, double* lap_dev);
 
 /* From scratch at positions R_dev [W][n_tot][3], without touching the walker state:
