@@ -1277,8 +1277,8 @@ msd_status msd_exc_histogram(const msd_ctx* c, int32_t spin, int64_t* out) {
 
 msd_status msd_copy_state(msd_ctx* c, int32_t item, int32_t spin, void* dst, int64_t* bytes) {
     if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_copy_state takes a single-system context");
-    if (c && c->canon && (item == 2 || item == 6 || item == 7 || item == 10))
-        return fail(c, MSD_ERR_ARG, "the canonical method keeps no table (items T, C, t, y0)");
+    if (c && c->canon && (item == 1 || item == 2 || item == 7 || item == 10))
+        return fail(c, MSD_ERR_ARG, "the canonical method keeps no table state (items Ainv, T, t, y0)");
     if (!c || spin < 0 || spin > 1 || item < 0 || item > 11) return fail(c, MSD_ERR_ARG, "invalid argument");
     if (item >= 8) {
         if (c->prop_elec < 0) return fail(c, MSD_ERR_STATE, "no msd_ratio proposal yet");
