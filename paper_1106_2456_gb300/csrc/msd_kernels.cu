@@ -83,7 +83,11 @@ __device__ __forceinline__ void copy_to_smem(TT* dst, const TT* __restrict__ src
 // whose left factor is generated on the fly.  Block tile: kOrbTP points x kOrbTJ orbitals, all
 // NC channels; basis functions in chunks of KC, the chunk of chi (every point and channel) and
 // of B staged in shared memory; each thread accumulates 2 points x NC channels x 4 orbitals.
-constexpr int kOrbTP = 32;
+#ifndef MSD_ORB_TP
+#define MSD_ORB_TP 32
+#endif
+constexpr int kOrbTP = MSD_ORB_TP;   // points per tile (16 threads per point group)
+constexpr int kOrbPPT = kOrbTP / 16;  // points per thread
 constexpr int kOrbTJ = 64;
 
 template <typename TO>
@@ -121,10 +125,10 @@ __device__ __forceinline__ void orbitals_tile(int P, int ppw, const double* __re
     constexpr int KC = orb_kc<TO>();
     __shared__ __align__(16) TO chi[KC][kOrbTP * NC];
     __shared__ __align__(16) TO Bs[KC][kOrbTJ];
-    const int tid = threadIdx.x, pg = tid >> 4, jg = tid & 15;  // points 2 pg, 2 pg + 1; orbitals 4 jg .. 4 jg + 3
-    TO acc[2][NC][4];
+    const int tid = threadIdx.x, pg = tid >> 4, jg = tid & 15;  // points kOrbPPT pg + q; orbitals 4 jg .. 4 jg + 3
+    TO acc[kOrbPPT][NC][4];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < kOrbPPT; ++q)
 #pragma unroll
         for (int a = 0; a < NC; ++a)
 #pragma unroll
@@ -152,10 +156,10 @@ __device__ __forceinline__ void orbitals_tile(int P, int ppw, const double* __re
 #pragma unroll
             for (int c = 0; c < 4; ++c) b[c] = Bs[kk][4 * jg + c];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < kOrbPPT; ++q)
 #pragma unroll
                 for (int a = 0; a < NC; ++a) {
-                    const TO x = chi[kk][(2 * pg + q) * NC + a];
+                    const TO x = chi[kk][(kOrbPPT * pg + q) * NC + a];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) acc[q][a][c] = fma(x, b[c], acc[q][a][c]);
                 }
@@ -163,8 +167,8 @@ __device__ __forceinline__ void orbitals_tile(int P, int ppw, const double* __re
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int p = p0 + 2 * pg + q;
+    for (int q = 0; q < kOrbPPT; ++q) {
+        const int p = p0 + kOrbPPT * pg + q;
         if (p >= P) continue;
 #pragma unroll
         for (int a = 0; a < NC; ++a)

@@ -204,11 +204,13 @@ def test_device_layout_plan(lib, label, kw):
         _check_records(lib, p, s, goff, dense)
 
 
-def test_device_layout_plan_fp64():
-    """FP64 tables: batches filled in sorted order, padding only at the end of each order."""
+@pytest.mark.parametrize("prec", [0, 2])
+def test_device_layout_plan_fp64(prec):
+    """FP64 tables and the canonical mode: batches filled in sorted order, padding only at
+    the end of each order."""
     lib = msd.load_library()
     p = wl.make_workload("medium", n_walkers=2).problem
-    s, keep = _struct(p, prec=0)
+    s, keep = _struct(p, prec=prec)
     out = np.zeros(32, dtype=np.int64)
     assert lib.msd_describe(ctypes.byref(s), out.ctypes.data) == 0
     d = out.reshape(2, 16)
