@@ -17,6 +17,9 @@ Functions and the passages they follow:
 * :func:`vmc_replay` -- Metropolis sweeps (Section II: a step moves one electron, a
   sweep moves each once), accept iff u < |Psi(R') / Psi(R)|^2 (no Jastrow factor).
 * :func:`lu_logdet` -- determinant by LU with partial pivoting.
+* :mod:`oracle.hamiltonian` -- the Pade-Jastrow factor, its ratio for a move, and the local
+  energy of Psi_T = exp(J) Psi_MD (numpy, from the definitions; Section VI runs VMC on such
+  a Jastrow-multideterminant wavefunction).
 
 Pins (tests/test_oracle_pins.py): Leibniz determinants, LAPACK determinants, finite
 differences of the basis, orbitals and Psi, the single-determinant reduction, the
@@ -209,12 +212,16 @@ class Oracle:
 
 
 def vmc_replay(oracle: Oracle, R0: np.ndarray, eta: np.ndarray, u: np.ndarray, tau: float,
-               n_steps: Optional[int] = None):
+               n_steps: Optional[int] = None, jastrow: Optional[Dict] = None):
     """Metropolis trajectory: step t moves electron t mod n_tot (up electrons first).
 
-    r' = r + tau * eta[t]; accept iff u[t] < |Psi(R') / Psi(R)|^2.  Returns per-step
-    records (elec, rnew, ratio, grad, lap, absum, accept) and the final positions.
+    r' = r + tau * eta[t]; accept iff u[t] < |Psi(R') / Psi(R)|^2, with Psi multiplied by
+    exp(J) when `jastrow` = dict(Z=..., b_ee=..., b_en=...) is given (``oracle.hamiltonian``).
+    Returns per-step records (elec, rnew, ratio, grad, lap, absum, accept) and the final
+    positions; `ratio` is that of Psi_MD alone, `ratio_T` that of the tested wavefunction.
     """
+    from . import hamiltonian
+
     p = oracle.p
     R = np.array(R0, dtype=np.float64, copy=True)
     W = R.shape[0]
@@ -225,8 +232,12 @@ def vmc_replay(oracle: Oracle, R0: np.ndarray, eta: np.ndarray, u: np.ndarray, t
         e = t % p.n_tot
         rnew = R[:, e, :] + tau * eta[t]
         ratio, new = oracle.ratio(R, e, rnew, cur)
-        acc = u[t] < ratio * ratio
-        recs.append(dict(elec=e, rnew=rnew.copy(), ratio=ratio, grad=new["grad"].copy(),
+        ratio_T = ratio
+        if jastrow is not None:
+            ratio_T = ratio * hamiltonian.jastrow_ratio(R, p.n_elec[0], e, rnew, p.nuc_xyz, np.asarray(jastrow["Z"]),
+                                                        jastrow.get("b_ee", 0.0), jastrow.get("b_en", 0.0))
+        acc = u[t] < ratio_T * ratio_T
+        recs.append(dict(elec=e, rnew=rnew.copy(), ratio=ratio, ratio_T=ratio_T, grad=new["grad"].copy(),
                          lap=new["lap"].copy(), absum=new["absum"].copy(), accept=acc.copy(),
                          logabs_new=new["logabs"].copy()))
         R[acc, e, :] = rnew[acc]
