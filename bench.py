@@ -601,6 +601,25 @@ def run_ours(args):
         line["e2e"] = {"value": job_rate(W, ws, e2e_steps, dt), "unit": UNIT, "steps": e2e_steps,
                        "h2d_bytes_per_step": W * 3 * 8 + W, "d2h_bytes_per_step": W * 5 * 8,
                        "path": "msd_ratio_host + msd_accept_host (pinned host buffers, synchronous)"}
+    # ---- VMC local energy (taken once per sweep of n_tot moves in a VMC run) ----
+    if args.eloc_calls > 0:
+        cm.set_hamiltonian(workloads.nuclear_charges(p), 1.0, 1.0)
+        eloc = torch.empty(W, dtype=torch.float64, device=dev)
+        cm.local_energy_into(eloc)  # the first call allocates its workspace
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.eloc_calls):
+            cm.local_energy_into(eloc)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms_le = max_over_ranks(a0.elapsed_time(a1), dist, dev) / args.eloc_calls
+        line["local_energy"] = {
+            "value": job_rate(W, ws, 1, ms_le * 1e-3), "unit": "walker local energies/s", "ms_per_call": ms_le,
+            "calls": args.eloc_calls, "vs_sweep": ms_le / (n_tot * ms / args.steps),
+            "what": "msd_local_energy, mixed: all-electron grad/lap (one cofactor scatter per spin), "
+                    "Pade-Jastrow (b_ee = b_en = 1) and Coulomb terms; vs_sweep = its time over one sweep of "
+                    "n_tot moves"}
     # ---- FP64 path on the same workload ----
     if not args.skip_fp64:
         cm.close()
@@ -655,6 +674,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=128)
     ap.add_argument("--cmp-steps", type=int, default=16)
+    ap.add_argument("--eloc-calls", type=int, default=5)
     ap.add_argument("--cpu-moves", type=int, default=30)
     ap.add_argument("--cpu-time-cap", type=float, default=25.0)
     ap.add_argument("--ref-time-cap", type=float, default=150.0)

@@ -27,8 +27,9 @@
  *   - Arrays are C-contiguous (row-major) with the stated shapes; W = n_walkers.
  *     Walker positions are [W][n_up + n_dn][3] doubles in bohr, up electrons first.
  *   - No call allocates after msd_init, except on first use msd_eval_batch (it creates a
- *     second walker state so that the main one is left untouched), msd_backward and
- *     msd_grad_lap with elec = -1 (their workspaces).
+ *     second walker state so that the main one is left untouched), msd_backward,
+ *     msd_grad_lap with elec = -1 and msd_local_energy (their workspaces), and
+ *     msd_set_hamiltonian (the nuclear charges).
  *   - Device-side numerical faults (a zero or non-finite pivot, a non-finite ratio)
  *     set a status word that msd_sync reports; host-side argument errors return
  *     MSD_ERR_ARG and leave the context unchanged.  msd_last_error explains the
@@ -258,6 +259,45 @@ msd_status msd_set_params(msd_ctx* ctx, const double* ci_host, const double* B_u
  * any stream capture the caller starts.  Nothing is allocated or freed by this call. */
 msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev,
                              double* grad_dev, double* lap_dev);
+
+/*
+ * VMC energy driver.  The paper runs VMC on Psi_T = exp(J) Psi_MD (Section VI) and leaves the
+ * Jastrow factor J to standard methods (Section II); these calls supply a simple one and the
+ * local energy of the electronic Hamiltonian (Hartree atomic units, clamped nuclei), so a
+ * Metropolis walk of Psi_T and its energy estimate run on the GPU.  Single-system contexts
+ * only; everything here is FP64 in both precision modes.
+ *
+ * Jastrow (two-body Pade form, cusp coefficients from Kato's conditions):
+ *   J = sum_{i<j} a_ij r_ij / (1 + b_ee r_ij) - sum_{i,I} Z_I r_iI / (1 + b_en r_iI),
+ *   a_ij = 1/2 for electrons of unlike spin and 1/4 for like spin.
+ * A parameter of 0 removes its term; msd_jastrow NULL (or both 0) means J = 0.
+ */
+typedef struct {
+    double b_ee;  /* >= 0: electron-electron term (0 = absent) */
+    double b_en;  /* >= 0: electron-nucleus term (0 = absent) */
+} msd_jastrow;
+
+/* Set the nuclear charges Z_host [n_nuc] (host, >= 0, in the order of msd_problem.nuc_xyz)
+ * and the Jastrow parameters (NULL = no Jastrow).  Computes the nuclear repulsion
+ * sum_{I<J} Z_I Z_J / R_IJ on the host.  May be called again to change them.  Synchronises
+ * the context's stream; the first call allocates n_nuc x 32 bytes.  MSD_ERR_ARG for a
+ * negative or non-finite value, or for two charged nuclei at the same point. */
+msd_status msd_set_hamiltonian(msd_ctx* ctx, const double* Z_host, const msd_jastrow* jas);
+
+/* Multiply ratio_dev [W] in place by exp(J(R') - J(R)) for the move of electron `elec` to
+ * rnew_dev [W][3] from the current positions, so that msd_ratio followed by this call gives
+ * Psi_T(R') / Psi_T(R) for msd_metropolis.  No state changes.  A no-op without a Jastrow term.
+ * MSD_ERR_STATE before msd_set_hamiltonian or msd_set_positions. */
+msd_status msd_jastrow_ratio(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev);
+
+/* Local energy E_L = (H Psi_T) / Psi_T of every walker at the current positions:
+ *   E_L = -1/2 sum_i lap_i Psi_T / Psi_T + sum_{i<j} 1/r_ij - sum_{i,I} Z_I / r_iI + V_nn,
+ *   lap_i Psi_T / Psi_T = lap_i D / D + lap_i J + |grad_i J|^2 + 2 grad_i J . grad_i D / D,
+ * with grad_i D / D and lap_i D / D of Psi_MD from the all-electron msd_grad_lap (elec = -1).
+ * eloc_dev [W]; parts_dev [W][4] = (kinetic, V_ee, V_en, V_nn) or NULL.  The first call
+ * allocates W x n_tot x 4 doubles of workspace.  MSD_ERR_STATE before msd_set_hamiltonian
+ * or msd_set_positions; MSD_ERR_ARG for the canonical method. */
+msd_status msd_local_energy(msd_ctx* ctx, double* eloc_dev, double* parts_dev);
 
 /* Release every device and host resource of the context (NULL is a no-op). */
 void msd_destroy(msd_ctx* ctx);

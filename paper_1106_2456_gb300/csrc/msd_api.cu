@@ -98,6 +98,14 @@ struct msd_ctx {
     int* term_id = nullptr;    // [n_det] internal down string of term I
     double* bw_M = nullptr;    // [W][n_max][N_max]
     double* bw_chi = nullptr;  // [W n_max][n_basis]
+    // VMC energy driver: nuclei, charges and Jastrow (msd_set_hamiltonian), and the
+    // all-electron gradient/laplacian workspace of msd_local_energy (allocated on first use)
+    std::vector<double> nuc_xyz;  // [n_nuc][3] host copy
+    bool ham_set = false;
+    double4* ham_nuc = nullptr;   // [n_nuc] (x, y, z, Z)
+    double ham_b_ee = 0.0, ham_b_en = 0.0, ham_vnn = 0.0;
+    double* le_grad = nullptr;    // [W][n_tot][3]
+    double* le_lap = nullptr;     // [W][n_tot]
     // batched uneven systems: one single-system context per system, run on kBatchStreams
     // internal streams forked from and joined back into `stream`
     std::vector<msd_ctx*> sub;
@@ -872,6 +880,7 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
         c->err = g_init_error;
         return bail(st);
     }
+    c->nuc_xyz.assign(p->nuc_xyz, p->nuc_xyz + 3 * (size_t)p->n_nuc);
     // basis
     std::vector<double4> bas(c->nb);
     for (int mu = 0; mu < c->nb; ++mu) {
@@ -1362,6 +1371,87 @@ msd_status msd_timing_stop(msd_ctx* c, double* sweep_ms, int64_t* sweep_launches
     c->timing = false;
     c->ev_used = 0;
     return MSD_OK;
+}
+
+msd_status msd_set_hamiltonian(msd_ctx* c, const double* Z_host, const msd_jastrow* jas) {
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_set_hamiltonian takes a single-system context");
+    if (!c || !Z_host) return fail(c, MSD_ERR_ARG, "NULL argument");
+    const int n_nuc = (int)(c->nuc_xyz.size() / 3);
+    const double b_ee = jas ? jas->b_ee : 0.0, b_en = jas ? jas->b_en : 0.0;
+    if (!std::isfinite(b_ee) || !std::isfinite(b_en) || b_ee < 0.0 || b_en < 0.0)
+        return fail(c, MSD_ERR_ARG, "Jastrow parameters must be finite and >= 0 (0 = term absent)");
+    std::vector<double4> nuc(n_nuc);
+    for (int I = 0; I < n_nuc; ++I) {
+        const double Z = Z_host[I];
+        if (!std::isfinite(Z) || Z < 0.0) return fail(c, MSD_ERR_ARG, "charge of nucleus %d must be finite and >= 0", I);
+        const double* A = c->nuc_xyz.data() + 3 * I;
+        nuc[I] = make_double4(A[0], A[1], A[2], Z);
+    }
+    // nuclear repulsion sum_{I<J} Z_I Z_J / R_IJ (a constant of the clamped nuclei)
+    double vnn = 0.0;
+    for (int I = 0; I < n_nuc; ++I)
+        for (int J = I + 1; J < n_nuc; ++J) {
+            const double dx = nuc[I].x - nuc[J].x, dy = nuc[I].y - nuc[J].y, dz = nuc[I].z - nuc[J].z;
+            const double zz = nuc[I].w * nuc[J].w;
+            if (zz == 0.0) continue;
+            const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (r == 0.0) return fail(c, MSD_ERR_ARG, "charged nuclei %d and %d coincide", I, J);
+            vnn += zz / r;
+        }
+    // the kernels of earlier calls may still read the charges: wait before overwriting them
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream synchronisation failed");
+    if (!c->ham_nuc) TRY(dalloc(c, &c->ham_nuc, (size_t)n_nuc));
+    if (cudaMemcpy(c->ham_nuc, nuc.data(), sizeof(double4) * n_nuc, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(c, MSD_ERR_CUDA, "upload of the nuclear charges failed");
+    c->ham_b_ee = b_ee;
+    c->ham_b_en = b_en;
+    c->ham_vnn = vnn;
+    c->ham_set = true;
+    return MSD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+msd::HamArgs ham_args(const msd_ctx* c) {
+    msd::HamArgs a;
+    a.W = c->W;
+    a.n_tot = c->n_tot;
+    a.n_up = c->sp[0].n;
+    a.n_nuc = (int)(c->nuc_xyz.size() / 3);
+    a.R = c->st.R;
+    a.nuc = c->ham_nuc;
+    a.b_ee = c->ham_b_ee;
+    a.b_en = c->ham_b_en;
+    a.vnn = c->ham_vnn;
+    return a;
+}
+}  // namespace
+
+extern "C" {
+
+msd_status msd_jastrow_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev) {
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_jastrow_ratio takes a single-system context");
+    if (!c || !rnew_dev || !ratio_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < 0 || elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if (!c->ham_set) return fail(c, MSD_ERR_STATE, "msd_set_hamiltonian has not been called");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    launch_jastrow_ratio(c->L(), ham_args(c), elec, rnew_dev, ratio_dev);
+    return check_launch(c, "Jastrow ratio");
+}
+
+msd_status msd_local_energy(msd_ctx* c, double* eloc_dev, double* parts_dev) {
+    if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_local_energy takes a single-system context");
+    if (!c || !eloc_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (!c->ham_set) return fail(c, MSD_ERR_STATE, "msd_set_hamiltonian has not been called");
+    if (!c->st.ready) return fail(c, MSD_ERR_STATE, "msd_set_positions has not been called");
+    const size_t W = c->W;
+    if (!c->le_grad) TRY(dalloc(c, &c->le_grad, W * c->n_tot * 3));
+    if (!c->le_lap) TRY(dalloc(c, &c->le_lap, W * c->n_tot));
+    TRY(msd_grad_lap(c, -1, c->le_grad, c->le_lap));
+    launch_local_energy(c->L(), ham_args(c), c->le_grad, c->le_lap, eloc_dev, parts_dev);
+    return check_launch(c, "local energy");
 }
 
 void msd_destroy(msd_ctx* c) {

@@ -206,6 +206,21 @@ void launch_chi(const Launch& L, int P, int ppw, const double* pos, long long ws
 // dB[mu][j] += sum_p chi[p][mu] Phib[p][j].
 void launch_dB(const Launch& L, int P, int nb, int N, const double* chi, const double* Phib, double* dB);
 
+// VMC energy driver (msd_vmc.cu): Jastrow factor and local energy, FP64.
+struct HamArgs {
+    int W, n_tot, n_up, n_nuc;
+    const double* R;      // [W][n_tot][3] current positions
+    const double4* nuc;   // [n_nuc] (x, y, z, Z)
+    double b_ee, b_en;    // Pade parameters of the Jastrow terms (<= 0: term absent)
+    double vnn;           // nuclear repulsion sum_{I<J} Z_I Z_J / R_IJ
+};
+// ratio[w] *= exp(J(R') - J(R)) for the move of electron elec to rnew[w].
+void launch_jastrow_ratio(const Launch& L, const HamArgs& a, int elec, const double* rnew, double* ratio);
+// eloc[w] and, if parts is non-NULL, parts[w] = (kinetic, V_ee, V_en, V_nn), from grad_i D / D
+// [W][n_tot][3] and lap_i D / D [W][n_tot] of the determinant part.
+void launch_local_energy(const Launch& L, const HamArgs& a, const double* gradD, const double* lapD, double* eloc,
+                         double* parts);
+
 // Fixed device scratch of msd_ratio_noalloc (msd_kernels.cu): its size, and its address on the
 // current device (looked up on the first call per device).
 constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;

@@ -67,6 +67,12 @@ def header_functions():
 _lib = None
 
 
+class Jastrow(ctypes.Structure):
+    """``msd_jastrow``: Pade parameters of the electron-electron and electron-nucleus terms
+    (0 removes a term)."""
+    _fields_ = [("b_ee", ctypes.c_double), ("b_en", ctypes.c_double)]
+
+
 def load_library():
     """Load libmsd.so (built by ``paper_1106_2456_gb300.build``); raise if it is missing."""
     global _lib
@@ -101,6 +107,9 @@ def load_library():
         "msd_copy_state": ([vp, i32, i32, vp, vp], i32),
         "msd_timing_start": ([vp], i32),
         "msd_timing_stop": ([vp, vp, vp, vp], i32),
+        "msd_set_hamiltonian": ([vp, vp, vp], i32),
+        "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
+        "msd_local_energy": ([vp, vp, vp], i32),
         "msd_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -300,6 +309,33 @@ class MSD:
     def propose(self, elec: int, eta: torch.Tensor, tau: float, out: torch.Tensor):
         self._check(self.lib.msd_propose(self.ctx, int(elec), _dptr(eta, torch.float64, (self.W, 3), "eta"),
                                          float(tau), _dptr(out, torch.float64, (self.W, 3), "out")))
+
+    # -- VMC energy driver ----------------------------------------------------------------
+    def set_hamiltonian(self, Z, b_ee: float = 0.0, b_en: float = 0.0):
+        """msd_set_hamiltonian: nuclear charges Z [n_nuc] and the Pade-Jastrow parameters
+        (0 removes a term; both 0 = no Jastrow)."""
+        z = np.ascontiguousarray(Z, dtype=np.float64)
+        if z.shape != (self.p.nuc_xyz.shape[0],):
+            raise ValueError(f"Z: expected shape ({self.p.nuc_xyz.shape[0]},)")
+        jas = Jastrow(float(b_ee), float(b_en))
+        self._check(self.lib.msd_set_hamiltonian(self.ctx, z.ctypes.data, ctypes.byref(jas)))
+
+    def jastrow_ratio_(self, elec: int, rnew: torch.Tensor, ratio: torch.Tensor):
+        """msd_jastrow_ratio: ratio [W] *= exp(J(R') - J(R)) for the move of `elec` to rnew."""
+        self._check(self.lib.msd_jastrow_ratio(self.ctx, int(elec), _dptr(rnew, torch.float64, (self.W, 3), "rnew"),
+                                               _dptr(ratio, torch.float64, (self.W,), "ratio")))
+
+    def local_energy_into(self, eloc: torch.Tensor, parts: Optional[torch.Tensor] = None):
+        self._check(self.lib.msd_local_energy(self.ctx, _dptr(eloc, torch.float64, (self.W,), "eloc"),
+                                              _dptr(parts, torch.float64, (self.W, 4), "parts")))
+
+    def local_energy(self, with_parts: bool = False):
+        """msd_local_energy: E_L [W] at the current positions and, if asked, the parts [W, 4]
+        (kinetic, V_ee, V_en, V_nn)."""
+        e = self._empty(self.W)
+        parts = self._empty(self.W, 4) if with_parts else None
+        self.local_energy_into(e, parts)
+        return (e, parts) if with_parts else e
 
     def metropolis(self, u: torch.Tensor, ratio: torch.Tensor, out: torch.Tensor):
         self._check(self.lib.msd_metropolis(self.ctx, _dptr(u, torch.float64, (self.W,), "u"),

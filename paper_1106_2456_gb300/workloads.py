@@ -329,6 +329,17 @@ def make_workload(label: str, n_walkers: Optional[int] = None, n_det: Optional[i
                     n_sweeps=cfg["sweeps"], label=label)
 
 
+def nuclear_charges(problem: Problem) -> np.ndarray:
+    """Charges Z_I for the local energy: water's (8, 1, 1) for the water system (10 electrons,
+    neutral); otherwise the n_tot electrons shared over the nuclei as evenly as integers allow,
+    the first nuclei taking the remainder, so that every synthetic system is neutral."""
+    n_nuc = problem.nuc_xyz.shape[0]
+    if problem.name == "water" and n_nuc == 3:
+        return np.array([8.0, 1.0, 1.0])
+    q, r = divmod(problem.n_tot, n_nuc)
+    return np.array([q + (1 if I < r else 0) for I in range(n_nuc)], dtype=np.float64)
+
+
 def feasible_terms(n: int, m: int, kmin: int, kmax: int) -> int:
     """Distinct (up string, down string) pairs of total excitation order kmin..kmax."""
     a = [math.comb(n, r) * math.comb(m, r) if r <= min(n, m, MAXK) else 0 for r in range(kmax + 1)]
