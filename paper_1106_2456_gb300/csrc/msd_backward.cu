@@ -69,6 +69,32 @@ __device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int
     }
 }
 
+// The same scatter from the adjugate as a whole: row q of cof(T_u) is column q of adj(T_u),
+// i.e. adj(T_u) e_q, which the pivoted elimination of the ratio sweep (adj_solve) gives for one
+// LU per column.  For K >= 5 that is far less work than K^2 separate (K-1) x (K-1) minors.
+template <int K, typename TT>
+__device__ __forceinline__ void scatter_adjugate(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], double cu,
+                                                 double* Tb) {
+    TT Tu[K * K];
+    int id[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        id[q] = q;
+#pragma unroll
+        for (int l = 0; l < K; ++l) Tu[q * K + l] = Ts[h[q] * m + p[l]];
+    }
+#pragma unroll 1
+    for (int q = 0; q < K; ++q) {
+        TT e[K], z[K], det;
+#pragma unroll
+        for (int j = 0; j < K; ++j) e[j] = j == q ? TT(1) : TT(0);
+        adj_solve<K, TT>(Tu, K, e, id, id, det, z);
+        double* row = Tb + h[q] * m;
+#pragma unroll
+        for (int l = 0; l < K; ++l) atomicAdd(row + p[l], cu * double(z[l]));
+    }
+}
+
 template <int K, typename TT>
 __device__ __forceinline__ void tbar_group(const ExcDev& g, const TT* Ts, int m, const TT* __restrict__ Cw,
                                            double* Tb) {
@@ -79,13 +105,25 @@ __device__ __forceinline__ void tbar_group(const ExcDev& g, const TT* Ts, int m,
         load_rec<K>(rec, j - j0, h, p);
         const double cu = double(Cw[j]);
         if (h[0] == kEmptyRecord || cu == 0.0) continue;
-        scatter_cofactors<K, TT>(Ts, m, h, p, cu, Tb);
+        if constexpr (K >= 5)
+            scatter_adjugate<K, TT>(Ts, m, h, p, cu, Tb);
+        else
+            scatter_cofactors<K, TT>(Ts, m, h, p, cu, Tb);
     }
 }
 
+// Orders 5-8 are rare: out of line, so that their registers do not limit orders 1-4.
+template <int K, typename TT>
+__device__ __noinline__ void tbar_group_outlined(const ExcDev& g, const TT* Ts, int m, const TT* __restrict__ Cw,
+                                                 double* Tb) {
+    tbar_group<K, TT>(g, Ts, m, Cw, Tb);
+}
+
+constexpr int kTbarThreads = 512;  // one block per SM (the table and its adjoint fill shared memory)
+
 // Writes Tbar / S into columns n..N-1 of M[w] (n x N, row stride N).
 template <typename TT>
-__global__ void __launch_bounds__(kBB) k_tbar(int n, int m, int N, ExcDev g, const TT* __restrict__ T,
+__global__ void __launch_bounds__(kTbarThreads, 1) k_tbar(int n, int m, int N, ExcDev g, const TT* __restrict__ T,
                                              const TT* __restrict__ C, const double* __restrict__ S,
                                              double* __restrict__ M) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -105,10 +143,10 @@ __global__ void __launch_bounds__(kBB) k_tbar(int n, int m, int N, ExcDev g, con
             case 2: tbar_group<2, TT>(g, Ts, m, Cw, Tb); break;
             case 3: tbar_group<3, TT>(g, Ts, m, Cw, Tb); break;
             case 4: tbar_group<4, TT>(g, Ts, m, Cw, Tb); break;
-            case 5: tbar_group<5, TT>(g, Ts, m, Cw, Tb); break;
-            case 6: tbar_group<6, TT>(g, Ts, m, Cw, Tb); break;
-            case 7: tbar_group<7, TT>(g, Ts, m, Cw, Tb); break;
-            case 8: tbar_group<8, TT>(g, Ts, m, Cw, Tb); break;
+            case 5: tbar_group_outlined<5, TT>(g, Ts, m, Cw, Tb); break;
+            case 6: tbar_group_outlined<6, TT>(g, Ts, m, Cw, Tb); break;
+            case 7: tbar_group_outlined<7, TT>(g, Ts, m, Cw, Tb); break;
+            case 8: tbar_group_outlined<8, TT>(g, Ts, m, Cw, Tb); break;
         }
     }
     __syncthreads();
@@ -286,14 +324,14 @@ void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, cons
         if (mixed) {
             cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             L.count();
-            k_tbar<float><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T),
+            k_tbar<float><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T),
                                                     static_cast<const float*>(C), S, M);
             L.count();
             k_tbar_tt<float><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const float*>(T), M);
         } else {
             cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             L.count();
-            k_tbar<double><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+            k_tbar<double><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
                                                      static_cast<const double*>(C), S, M);
             L.count();
             k_tbar_tt<double><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const double*>(T), M);
@@ -330,12 +368,12 @@ void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const 
     if (mixed) {
         cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         L.count();
-        k_tbar<float><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T), static_cast<const float*>(C),
+        k_tbar<float><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T), static_cast<const float*>(C),
                                                 S, M);
     } else {
         cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         L.count();
-        k_tbar<double><<<W, kBB, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+        k_tbar<double><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
                                                  static_cast<const double*>(C), S, M);
     }
 }

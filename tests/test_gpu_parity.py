@@ -124,7 +124,16 @@ def test_one_walker_one_electron_per_spin():
 def test_all_electron_grad_lap(label, W):
     """msd_grad_lap for every electron (one cofactor scatter per spin) against the oracle,
     FP64 and mixed, at the initial positions and after moves."""
-    w = wl.make_workload(label, n_walkers=W)
+    _check_all_electron(wl.make_workload(label, n_walkers=W), W)
+
+
+def test_all_electron_grad_lap_orders_1_to_8():
+    """The cofactor scatter of orders 5-8 (adjugate by pivoted elimination) on every electron."""
+    w = wl.custom_workload((11, 9), (25, 26), 300, wl.uniform_orders(1, 8), W=3, n_nuc=4, seed=11, K=7)
+    _check_all_electron(w, 3)
+
+
+def _check_all_electron(w, W):
     p = w.problem
     orc = oracle.Oracle(p)
     for prec in ("fp64", "mixed"):
