@@ -17,6 +17,48 @@ import torch
 from .msd import MSD
 
 
+def blocking_stderr(series, min_blocks: int = 16) -> float:
+    """Standard error of the mean of a serially correlated series by blocking (Flyvbjerg and
+    Petersen, J. Chem. Phys. 91, 461 (1989)).
+
+    Neighbouring values are averaged in pairs, level after level.  The naive error of the
+    blocked series grows until the blocks outlast the correlation time, then levels off.
+    Returns the largest naive estimate over the levels that keep at least `min_blocks`
+    blocks, and always includes level 0.  With fewer than 2 values the error is undefined
+    (nan).
+    """
+    x = np.asarray(series, dtype=np.float64).ravel()
+    if x.size < 2:
+        return float("nan")
+    best = float(x.std(ddof=1) / np.sqrt(x.size))
+    while x.size // 2 >= min_blocks:
+        h = x.size // 2
+        x = 0.5 * (x[0:2 * h:2] + x[1:2 * h:2])
+        best = max(best, float(x.std(ddof=1) / np.sqrt(x.size)))
+    return best
+
+
+def combine_replicas(sweep_sums: torch.Tensor, n_walkers: int, n_accepted: float, n_proposed: float):
+    """Per-sweep mean energies over the walkers of every replica, and the overall acceptance.
+
+    Each process runs its own walkers (independent Markov chains); when torch.distributed is
+    initialised, one all-reduce of [per-sweep energy sums, walker count, accepted, proposed]
+    per run combines them.  This is the only exchange of a replicated run, and it lies
+    outside the moves.  The tensor must be on the device the process group uses.  Returns
+    (means [n_sweeps], acceptance).
+    """
+    v = torch.cat([sweep_sums.to(torch.float64).ravel(),
+                   torch.tensor([float(n_walkers), float(n_accepted), float(n_proposed)], dtype=torch.float64,
+                                device=sweep_sums.device)])
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(v)
+    k = sweep_sums.numel()
+    means = v[:k] / v[k]
+    acc = float(v[k + 1] / v[k + 2]) if float(v[k + 2]) > 0 else float("nan")
+    return means, acc
+
+
 class VMC:
     """Drive a walker population of an :class:`MSD` context.
 
@@ -67,18 +109,20 @@ class VMC:
 
     def run(self, n_sweeps: int, n_equil: int = 0) -> Dict[str, float]:
         """n_equil sweeps without measurement, then n_sweeps with E_L after each.  Returns the
-        mean energy, its standard error from the per-sweep walker averages (treated as
-        independent), and the acceptance ratio of the measured sweeps."""
+        mean energy over all walkers (of every replica, when torch.distributed is initialised),
+        its standard error by blocking the per-sweep means (successive sweeps are correlated),
+        and the acceptance ratio of the measured sweeps."""
         for _ in range(n_equil):
             self.sweep()
         self.n_acc.zero_()
         self.n_prop = 0
-        means = []
+        sums = []
         for _ in range(n_sweeps):
             self.sweep()
-            means.append(self.energy().mean())
-        m = torch.stack(means).cpu().numpy() if means else np.zeros(0)
-        err = float(m.std(ddof=1) / np.sqrt(len(m))) if len(m) > 1 else float("nan")
-        acc = float(self.n_acc.sum().item() / max(1, self.n_prop * self.ctx.W))
-        return dict(energy=float(m.mean()) if len(m) else float("nan"), stderr=err, acceptance=acc,
-                    sweeps=int(n_sweeps))
+            sums.append(self.energy().sum())
+        if not sums:
+            return dict(energy=float("nan"), stderr=float("nan"), acceptance=float("nan"), sweeps=0)
+        means, acc = combine_replicas(torch.stack(sums), self.ctx.W, float(self.n_acc.sum().item()),
+                                      float(self.n_prop * self.ctx.W))
+        m = means.cpu().numpy()
+        return dict(energy=float(m.mean()), stderr=blocking_stderr(m), acceptance=acc, sweeps=int(n_sweeps))
