@@ -294,7 +294,8 @@ msd_status msd_jastrow_ratio(msd_ctx* ctx, int32_t elec, const double* rnew_dev,
  *   E_L = -1/2 sum_i lap_i Psi_T / Psi_T + sum_{i<j} 1/r_ij - sum_{i,I} Z_I / r_iI + V_nn,
  *   lap_i Psi_T / Psi_T = lap_i D / D + lap_i J + |grad_i J|^2 + 2 grad_i J . grad_i D / D,
  * with grad_i D / D and lap_i D / D of Psi_MD from the all-electron msd_grad_lap (elec = -1).
- * eloc_dev [W]; parts_dev [W][4] = (kinetic, V_ee, V_en, V_nn) or NULL.  The first call
+ * eloc_dev [W]; parts_dev [W][4] = (kinetic, V_ee, V_en, V_nn) or NULL.  Two particles at
+ * the same point give an infinite E_L for that walker (no status is set).  The first call
  * allocates W x n_tot x 4 doubles of workspace.  MSD_ERR_STATE before msd_set_hamiltonian
  * or msd_set_positions; MSD_ERR_ARG for the canonical method. */
 msd_status msd_local_energy(msd_ctx* ctx, double* eloc_dev, double* parts_dev);
