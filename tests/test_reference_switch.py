@@ -118,3 +118,11 @@ def test_order_limit_is_enforced():
                             [ref, a, b], [ref], [0, 1, 2], [0, 0, 0], [1.0, 0.5, 0.25])
     with pytest.raises(ValueError):
         reference.switch_reference(p, 1)
+
+
+def test_heaviest_term_is_the_largest_non_reference_term():
+    p = _problems()[1].problem
+    I = reference.heaviest_term(p)
+    assert not (p.det_up[I] == 0 and p.det_dn[I] == 0)
+    others = [abs(p.ci[J]) for J in range(p.n_det) if not (p.det_up[J] == 0 and p.det_dn[J] == 0)]
+    assert abs(p.ci[I]) == max(others)

@@ -68,3 +68,12 @@ def test_generator_is_deterministic():
     assert np.array_equal(a.problem.ci, b.problem.ci)
     assert np.array_equal(a.R0, b.R0)
     assert np.array_equal(a.problem.exc_holes[1], b.problem.exc_holes[1])
+
+
+def test_nuclear_charges_make_every_system_neutral():
+    w = wl.make_workload("water", n_walkers=1)
+    assert list(wl.nuclear_charges(w.problem)) == [8.0, 1.0, 1.0]
+    for n, n_nuc in (((5, 4), 4), ((7, 7), 3), ((3, 2), 6)):
+        c = wl.custom_workload(n, (n[0] + 4, n[1] + 4), 10, wl.uniform_orders(1, 2), W=1, n_nuc=n_nuc, seed=2)
+        Z = wl.nuclear_charges(c.problem)
+        assert Z.sum() == sum(n) and Z.max() - Z.min() <= 1 and np.all(Z == np.round(Z))
