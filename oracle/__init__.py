@@ -74,7 +74,7 @@ def _load():
         lib.orc_eval.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         lib.orc_eval.restype = i32
         lib.orc_eval_batch.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp]
-        lib.orc_dlogpsi.argtypes = [vp, vp, vp, vp, vp]
+        lib.orc_dlogpsi.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.orc_dlogpsi.restype = i32
         lib.orc_num_threads.restype = i32
         _lib = lib
@@ -199,15 +199,23 @@ class Oracle:
         ratio = new["sign"] * cur["sign"] * np.exp(new["logabs"] - cur["logabs"])
         return ratio, new
 
-    def dlogpsi(self, R: np.ndarray):
-        """d log|Psi| / d c [n_det] and d log|Psi| / d B_s [n_basis, n_orb] per spin, one walker."""
+    def dlogpsi(self, R: np.ndarray, with_scale: bool = False):
+        """d log|Psi| / d c [n_det] and d log|Psi| / d B_s [n_basis, n_orb] per spin, one walker.
+
+        with_scale=True also returns the per-entry cancellation scale of each d/dB_s (the sum of
+        the absolute values of the terms of Jacobi's formula that form it)."""
         R = np.ascontiguousarray(R, np.float64).reshape(self.p.n_tot, 3)
         dci = np.zeros(self.p.n_det)
         dB0 = np.zeros((self.p.n_basis, self.p.n_orb[0]))
         dB1 = np.zeros((self.p.n_basis, self.p.n_orb[1]))
-        rc = self._lib.orc_dlogpsi(self._sp, _ptr(R), _ptr(dci), _ptr(dB0), _ptr(dB1))
+        s0 = np.zeros_like(dB0) if with_scale else None
+        s1 = np.zeros_like(dB1) if with_scale else None
+        rc = self._lib.orc_dlogpsi(self._sp, _ptr(R), _ptr(dci), _ptr(dB0), _ptr(dB1),
+                                   _ptr(s0) if with_scale else None, _ptr(s1) if with_scale else None)
         if rc:
             raise FloatingPointError("Psi is exactly zero at this configuration")
+        if with_scale:
+            return dci, (dB0, dB1), (s0, s1)
         return dci, (dB0, dB1)
 
 

@@ -339,9 +339,14 @@ void orc_eval_batch(const orc_problem* p, int W, const double* R, int elec, cons
  *   d log|Psi| / d B_s[mu][j] = sum_I c_I det M_other,I sum_{r, c: col(c) = j}
  *                               chi_mu(r_r) det M_s,I (M_s,I^{-1})(c, r) / Psi.
  * dci [n_det]; dB[s] [n_basis][n_orb[s]] (per spin; a restricted B gets their sum).
+ * dB_scale[s] (optional, same shape): the same double sum with every term replaced by its
+ * absolute value, |c_I det M_other,I| |chi_mu(r_r)| |det M_s,I (M_s,I^{-1})(c, r)| / |Psi|:
+ * the size of the terms that cancel in dB[s], against which its rounding is judged.
  */
-int orc_dlogpsi(const orc_problem* p, const double* R, double* dci, double* dB0, double* dB1) {
+int orc_dlogpsi(const orc_problem* p, const double* R, double* dci, double* dB0, double* dB1, double* dB0_scale,
+                double* dB1_scale) {
     double* dB[2] = {dB0, dB1};
+    double* dBs[2] = {dB0_scale, dB1_scale};
     const int nb = p->n_basis;
     double* l[2];
     double* sg[2];
@@ -386,15 +391,19 @@ int orc_dlogpsi(const orc_problem* p, const double* R, double* dci, double* dB0,
         const int n = p->n_elec[s], N = p->n_orb[s], ne = p->n_exc[s];
         const int so = 1 - s;
         double* wgt = (double*)calloc((size_t)ne, sizeof(double));
+        double* wabs = (double*)calloc((size_t)ne, sizeof(double));
         double Ls = -INFINITY;
         for (int u = 0; u < ne; ++u) if (l[s][u] > Ls) Ls = l[s][u];
         for (int64_t I = 0; I < p->n_det; ++I) {
             const int us = s ? p->det_dn[I] : p->det_up[I];
             const int uo = s ? p->det_up[I] : p->det_dn[I];
             wgt[us] += p->ci[I] * sg[so][uo] * exp(l[so][uo] + Ls - Lmax);
+            wabs[us] += fabs(p->ci[I]) * exp(l[so][uo] + Ls - Lmax);
         }
         /* phibar[r][j] = sum_u wgt[u] sum_{c: col_u(c) = j} cof_u(r, c) e^{-Ls} / S */
         double* phibar = (double*)calloc((size_t)n * N + 1, sizeof(double));
+        /* the same sum with every term by its absolute value: the cancellation scale of phibar */
+        double* phiabs = (double*)calloc((size_t)n * N + 1, sizeof(double));
 #pragma omp parallel
         {
             double* A = (double*)malloc(sizeof(double) * ((size_t)n * n + 1));
@@ -404,30 +413,45 @@ int orc_dlogpsi(const orc_problem* p, const double* R, double* dci, double* dB0,
             int* perm = (int*)malloc(sizeof(int) * ((size_t)n + 1));
             int* cols = (int*)malloc(sizeof(int) * ((size_t)n + 1));
             double* loc = (double*)calloc((size_t)n * N + 1, sizeof(double));
+            double* lab = (double*)calloc((size_t)n * N + 1, sizeof(double));
 #pragma omp for schedule(dynamic, 16)
             for (int u = 0; u < ne; ++u) {
-                if (wgt[u] == 0.0 || sg[s][u] == 0.0) continue;
+                if (wabs[u] == 0.0 || sg[s][u] == 0.0) continue;
                 string_columns(p, s, u, cols);
                 for (int r = 0; r < n; ++r)
                     for (int c = 0; c < n; ++c) A[(size_t)r * n + c] = rows[s][(size_t)r * N + cols[c]];
                 if (lu_inverse(n, A, lu, perm, inv, col)) continue;
                 const double detw = wgt[u] * sg[s][u] * exp(l[s][u] - Ls) / S;
+                const double deta = wabs[u] * exp(l[s][u] - Ls) / fabs(S);
                 for (int r = 0; r < n; ++r)
-                    for (int c = 0; c < n; ++c)
+                    for (int c = 0; c < n; ++c) {
                         loc[(size_t)r * N + cols[c]] += detw * inv[(size_t)c * n + r];
+                        lab[(size_t)r * N + cols[c]] += deta * fabs(inv[(size_t)c * n + r]);
+                    }
             }
 #pragma omp critical
-            for (size_t q = 0; q < (size_t)n * N; ++q) phibar[q] += loc[q];
-            free(A); free(lu); free(inv); free(col); free(perm); free(cols); free(loc);
+            for (size_t q = 0; q < (size_t)n * N; ++q) {
+                phibar[q] += loc[q];
+                phiabs[q] += lab[q];
+            }
+            free(A); free(lu); free(inv); free(col); free(perm); free(cols); free(loc); free(lab);
         }
         for (int mu = 0; mu < nb; ++mu)
             for (int j = 0; j < N; ++j) {
                 double acc = 0.0;
                 for (int r = 0; r < n; ++r) acc += chi_rows[s][(size_t)r * nb + mu] * phibar[(size_t)r * N + j];
                 dB[s][(size_t)mu * N + j] = acc;
+                if (dBs[s]) {
+                    double sa = 0.0;
+                    for (int r = 0; r < n; ++r)
+                        sa += fabs(chi_rows[s][(size_t)r * nb + mu]) * phiabs[(size_t)r * N + j];
+                    dBs[s][(size_t)mu * N + j] = sa;
+                }
             }
         free(wgt);
+        free(wabs);
         free(phibar);
+        free(phiabs);
     }
     for (int s = 0; s < 2; ++s) { free(l[s]); free(sg[s]); free(rows[s]); free(chi_rows[s]); }
     return 0;

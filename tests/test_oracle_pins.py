@@ -350,3 +350,130 @@ def test_adjoint_invariants_and_fd():
             fp = oracle.Oracle(wl.dataclasses.replace(p, B=tuple(Bp))).eval(R)["logabs"][0]
             fm = oracle.Oracle(wl.dataclasses.replace(p, B=tuple(Bm))).eval(R)["logabs"][0]
             assert dB[s][mu, j] == pytest.approx((fp - fm) / (2 * h), rel=1e-5, abs=1e-8)
+
+
+# ---------------------------------------------------------------------------------
+# reference Slater matrices and their condition number (the kappa of every parity bar)
+# ---------------------------------------------------------------------------------
+
+def _known_condition_problem(R, targets, seed=5):
+    """A problem whose reference Slater matrix of spin s at R is exactly targets[s].
+
+    A_0 = X_s B_s with X_s[r, mu] = chi_mu(r_r) (the basis at the spin's electrons, from the
+    oracle's basis evaluator, pinned above), so B_s = pinv(X_s) targets[s] reproduces any
+    n_s x n_s target while n_s <= n_basis.
+    """
+    rng = np.random.default_rng(seed)
+    nuc = wl.chain_nuclei(rng, 3)
+    bc, blm, bal = wl.gaussian_basis(rng, 3)
+    n = (targets[0].shape[0], targets[1].shape[0])
+    probe = wl.explicit_problem(nuc, bc, blm, bal, (np.eye(len(bc))[:, :n[0]], np.eye(len(bc))[:, :n[1]]), n,
+                                [((), ())], [((), ())], [0], [0], [1.0])
+    o = oracle.Oracle(probe)
+    B = []
+    for s in range(2):
+        off = 0 if s == 0 else n[0]
+        X = np.stack([o.basis(R[off + r])[0] for r in range(n[s])])  # [n_s, n_basis]
+        B.append(np.linalg.pinv(X) @ targets[s])
+    return wl.explicit_problem(nuc, bc, blm, bal, tuple(B), n, [((), ())], [((), ())], [0], [0], [1.0])
+
+
+def _matrix_with_condition(rng, n, kappa):
+    """Q diag(s) V^T with singular values log-spaced from 1 to 1/kappa: 2-norm condition kappa."""
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q @ np.diag(np.logspace(0.0, -np.log10(kappa), n)) @ V.T
+
+
+def test_slater_and_reference_condition_known_kappa():
+    """Oracle.slater rebuilds a chosen matrix per spin (a wrong down-spin row offset or a
+    transposed A_0 fails), and reference_condition returns the 2-norm condition number of the
+    worse spin, known here by construction, and of the moved spin's matrix at R'."""
+    rng = np.random.default_rng(17)
+    n_up, n_dn = 4, 3
+    R = rng.standard_normal((n_up + n_dn, 3)) * 1.2
+    targets = (_matrix_with_condition(rng, n_up, 40.0), _matrix_with_condition(rng, n_dn, 900.0))
+    p = _known_condition_problem(R, targets)
+    o = oracle.Oracle(p)
+    for s in range(2):
+        A = o.slater(s, R)
+        assert np.allclose(A, targets[s], rtol=0, atol=1e-9 * np.abs(targets[s]).max())
+        # rows are electrons: a transposed or row-shifted matrix differs from the target
+        assert not np.allclose(A.T, targets[s], atol=1e-6)
+    kap = o.reference_condition(R)
+    assert kap == pytest.approx(900.0, rel=1e-6)
+    # swap the roles: the up spin ill-conditioned, the down spin not
+    targets2 = (_matrix_with_condition(rng, n_up, 2.5e4), _matrix_with_condition(rng, n_dn, 3.0))
+    o2 = oracle.Oracle(_known_condition_problem(R, targets2))
+    assert o2.reference_condition(R) == pytest.approx(2.5e4, rel=1e-6)
+    # moved electron: the moved spin's matrix at R' is A_0 with the electron's row replaced by
+    # the orbitals at r', built here from the orbital evaluator row by row
+    e = 5  # second down electron, row 1 of the down matrix
+    rnew = R[e] + np.array([0.3, -0.2, 0.1])
+    R2 = R.copy()
+    R2[e] = rnew
+    row = np.stack([o.orbitals(1, R2[n_up + r])[0][:n_dn] for r in range(n_dn)])
+    want = max(40.0, 900.0, np.linalg.cond(row))
+    assert o.reference_condition(R, e, rnew) == pytest.approx(want, rel=1e-9)
+    # an up-electron move is judged on the up matrix at R' (the down one is unchanged)
+    R3 = R.copy()
+    R3[1] = R[1] + np.array([-0.4, 0.2, 0.5])
+    rowu = np.stack([o.orbitals(0, R3[r])[0][:n_up] for r in range(n_up)])
+    assert o.reference_condition(R, 1, R3[1]) == pytest.approx(max(900.0, np.linalg.cond(rowu)), rel=1e-9)
+
+
+@pytest.mark.parametrize("label", ["water", "medium"])
+def test_slater_matches_orbital_rows_and_determinant(label):
+    """On the generated workloads: Oracle.slater(s, R) stacks the occupied orbitals of the
+    spin's own electrons (down electrons start at n_up), and det A_up det A_dn equals the
+    single-determinant Psi that the oracle's LU evaluation gives independently."""
+    w = wl.make_workload(label, n_walkers=2)
+    p = w.problem
+    single = wl.explicit_problem(p.nuc_xyz, p.bas_center, p.bas_lm, p.bas_alpha, p.B, p.n_elec,
+                                 [((), ())], [((), ())], [0], [0], [1.0])
+    o = oracle.Oracle(single)
+    R = w.R0[1]
+    logs = 0.0
+    sign = 1.0
+    for s in range(2):
+        n = p.n_elec[s]
+        off = 0 if s == 0 else p.n_elec[0]
+        A = o.slater(s, R)
+        rows = np.stack([o.orbitals(s, R[off + r])[0][:n] for r in range(n)])
+        assert np.array_equal(A, rows)
+        sg, ld = np.linalg.slogdet(A)
+        logs += ld
+        sign *= sg
+        assert o.reference_condition(R) >= np.linalg.cond(A) * (1 - 1e-12)
+    ev = o.eval(R)
+    assert ev["logabs"][0] == pytest.approx(logs, rel=1e-11, abs=1e-11)
+    assert ev["sign"][0] == sign
+
+
+def test_adjoint_cancellation_scale():
+    """The per-entry scale the adjoint parity bars use: it bounds |d log|Psi| / dB| entry by entry
+    (triangle inequality) and, for a single determinant, is sum_r |chi_mu(r_r)| |A_0^{-1}[j, r]|
+    (Jacobi: d log|det A_0| / dA_0[r, j] = A_0^{-1}[j, r]; zero on the virtual orbitals)."""
+    w = wl.make_workload("water", n_walkers=1, n_det=40)
+    p = w.problem
+    R = w.R0[0]
+    dci, dB, sc = oracle.Oracle(p).dlogpsi(R, with_scale=True)
+    for s in range(2):
+        assert np.all(sc[s] >= np.abs(dB[s]) * (1 - 1e-12))
+        assert np.all(sc[s] > 0)
+    single = wl.explicit_problem(p.nuc_xyz, p.bas_center, p.bas_lm, p.bas_alpha, p.B, p.n_elec,
+                                 [((), ())], [((), ())], [0], [0], [-2.0])
+    o = oracle.Oracle(single)
+    _, dB1, sc1 = o.dlogpsi(R, with_scale=True)
+    for s in range(2):
+        n = p.n_elec[s]
+        off = 0 if s == 0 else p.n_elec[0]
+        X = np.stack([o.basis(R[off + r])[0] for r in range(n)])  # [n, n_basis]
+        Ainv = np.linalg.inv(o.slater(s, R))                       # [j, r]
+        want = np.zeros_like(sc1[s])
+        want[:, :n] = np.abs(X).T @ np.abs(Ainv).T
+        assert np.allclose(sc1[s], want, rtol=1e-10, atol=1e-14)
+        # and the value itself: sum_r chi_mu(r_r) A_0^{-1}[j, r]
+        val = np.zeros_like(dB1[s])
+        val[:, :n] = X.T @ Ainv.T
+        assert np.allclose(dB1[s], val, rtol=1e-9, atol=1e-12)
