@@ -10,9 +10,16 @@ laplacian) is compared element by element:
 where scale_X = sum_I |c_I X_I| / |Psi| is the cancellation scale of the CI sum that forms
 X (the oracle returns it), so a result that is a small difference of large terms is judged
 against the size of the terms, as FP64 rounding of those terms allows nothing tighter.
+
+Every result is also classified (``bar_report``): whether it meets the flat bar (1e-10 for
+FP64, i.e. the kappa-independent constant), whether it needed the kappa scaling to pass, and
+its plain relative error |X_gpu - X_oracle| / |X_oracle|.  Setting MSD_PARITY_REPORT to a file
+path appends one JSON line per replay with that classification.
 """
 from __future__ import annotations
 
+import json
+import os
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -31,14 +38,53 @@ U32 = 2.0 ** -24
 
 
 def tol_fp64(kappa):
-    """FP64 bar: 1e-10 while cond(A_0) <= 3e3; beyond that the table method's error grows
-    with cond(A_0) (every quantity passes through A_0^{-1}; Section V), ~3e-14 * kappa."""
+    """FP64 bar: 1e-10, the flat bar, while cond(A_0) <= 3e3; beyond that it may grow as
+    1e-10 kappa / 3e3 (every quantity of the table method passes through A_0^{-1}; Section V
+    names this instability), and the tests cap how many results may use that allowance
+    (KAPPA_ONLY_SHARE).  Measured on the FP64 water walk the error does not grow with kappa
+    (max 1e-11 up to kappa = 1e6); one result in about 1e5 of the GPU tests needs the allowance."""
     return 1e-10 * np.maximum(1.0, np.asarray(kappa) / 3e3)
 
 
 def tol_mixed(kappa):
-    """Mixed bar: FP32 rounding amplified by cond(A_0): 1e3 * u_fp32 * max(kappa, 10)."""
-    return 1e3 * U32 * np.maximum(np.asarray(kappa), 10.0)
+    """Mixed bar: 1e-3, the flat bar, or 10 u_fp32 kappa where that is larger (FP32 rounding of
+    the orbitals and the table amplified by cond(A_0) through T = A_0^{-1} Phi_virt).  Measured
+    on the mixed water walk the error stays below 3e-4 at every kappa up to 1e6."""
+    return np.maximum(1e-3, 10.0 * U32 * np.asarray(kappa))
+
+
+FLAT = {"fp64": 1e-10, "mixed": 1e-3}
+# Largest share of a test's results that may pass only through the kappa allowance of the bar.
+KAPPA_ONLY_SHARE = {"fp64": 1e-3, "mixed": 2e-2}
+
+
+def bar_report(out, precision: str, label: str = "") -> Dict:
+    """Classify every compared result of a replay: how many meet the flat bar (FLAT), how many
+    pass only through the kappa allowance, how many fail; the worst plain relative error overall
+    and among well-conditioned results with little cancellation (kappa <= 3e3, scale_X <= 10 |X|),
+    and the largest kappa seen."""
+    flat = FLAT[precision]
+    rep = {"label": label, "precision": precision}
+    for key in ("ratio", "grad", "lap"):
+        es = np.concatenate(out["rec"][key]["scaled"]) if out["rec"][key]["scaled"] else np.zeros(0)
+        ep = np.concatenate(out["rec"][key]["plain"]) if out["rec"][key]["plain"] else np.zeros(0)
+        kp = np.concatenate(out["rec"][key]["kappa"]) if out["rec"][key]["kappa"] else np.zeros(0)
+        sc = np.concatenate(out["rec"][key]["canc"]) if out["rec"][key]["canc"] else np.zeros(0)
+        tol = (tol_mixed if precision == "mixed" else tol_fp64)(kp)
+        flat_ok = es <= flat
+        ok = es <= tol
+        plain_sel = (kp <= 3e3) & (sc <= 10.0)
+        rep[key] = {"n": int(es.size), "flat_pass": int(flat_ok.sum()), "kappa_only": int((ok & ~flat_ok).sum()),
+                    "fail": int((~ok).sum()), "max_scaled": float(es.max(initial=0.0)),
+                    "max_plain": float(ep.max(initial=0.0)),
+                    "n_plain_well": int(plain_sel.sum()),
+                    "max_plain_well": float(ep[plain_sel].max(initial=0.0)),
+                    "max_kappa": float(kp.max(initial=0.0))}
+    path = os.environ.get("MSD_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(rep) + "\n")
+    return rep
 
 
 def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = None, refresh_K: Optional[int] = None,
@@ -61,7 +107,7 @@ def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = No
     # initial log|Psi| and sign
     _, la, sg = ctx.get_state()
     out = dict(ratio=[], grad=[], lap=[], logabs=[], sign_ok=[], accept=[], ratio_n=[], grad_n=[], lap_n=[],
-               kappa=[])
+               kappa=[], rec={k: dict(scaled=[], plain=[], kappa=[], canc=[]) for k in ("ratio", "grad", "lap")})
     # |d log|Psi|| is the relative error of Psi: judged like the ratio, against the bar at the
     # walker's conditioning times the cancellation scale of the CI sum
     kap0 = np.array([orc.reference_condition(Rh[w_]) for w_ in idx])
@@ -85,9 +131,20 @@ def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = No
         er = rel_err(g_r[idx], r_or, ab[:, 0] * np.abs(r_or))
         eg = rel_err(g_g[idx], new["grad"], ab[:, 1:4]).max(axis=1)
         el = rel_err(g_l[idx], new["lap"], ab[:, 4])
+        tiny = 1e-300
+        plain = {"ratio": np.abs(g_r[idx] - r_or) / np.maximum(np.abs(r_or), tiny),
+                 "grad": (np.abs(g_g[idx] - new["grad"]) / np.maximum(np.abs(new["grad"]), tiny)).max(axis=1),
+                 "lap": np.abs(g_l[idx] - new["lap"]) / np.maximum(np.abs(new["lap"]), tiny)}
+        canc = {"ratio": ab[:, 0],
+                "grad": (ab[:, 1:4] / np.maximum(np.abs(new["grad"]), tiny)).max(axis=1),
+                "lap": ab[:, 4] / np.maximum(np.abs(new["lap"]), tiny)}
         for key, v in (("ratio", er), ("grad", eg), ("lap", el)):
             out[key].append(float(v.max()))
             out[key + "_n"].append(float((v / tol).max()))
+            out["rec"][key]["scaled"].append(v)
+            out["rec"][key]["plain"].append(plain[key])
+            out["rec"][key]["kappa"].append(kap)
+            out["rec"][key]["canc"].append(canc[key])
         out["kappa"].append(float(kap.max()))
         acc = u[t] < g_r * g_r
         out["accept"].append(float(acc.mean()))

@@ -46,3 +46,21 @@ def test_sweep_work_model():
     f2, b2 = bench.sweep_work(p, 0, 20, True, 400)
     assert f2 == 2 * f and b2 > b and b2 < 2 * b + 1  # records are read once per launch
     assert np.isfinite(f) and f > 0
+
+
+def test_traffic_record_is_dropped_when_the_kernel_changed(tmp_path, monkeypatch):
+    """The roofline's measured DRAM traffic comes from profiles/traffic.json only while the sweep
+    kernel's sources hash to the value recorded with the capture."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    path = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(path))
+    assert bench.profiled_traffic(True) is None
+    rec = {"dram_bytes_per_walker": 250000.0, "walkers": 1024, "source_hash": bench.sweep_source_hash()}
+    path.write_text(json.dumps({"k_ratio_mixed": rec}))
+    got = bench.profiled_traffic(True)
+    assert got["dram_bytes_per_walker"] == 250000.0 and got["walkers"] == 1024
+    assert bench.profiled_traffic(False) is None
+    path.write_text(json.dumps({"k_ratio_mixed": dict(rec, source_hash="0" * 16)}))
+    assert bench.profiled_traffic(True) is None

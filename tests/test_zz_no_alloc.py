@@ -85,3 +85,75 @@ def test_oversize_is_refused():
     ctx.ratio_noalloc_into(0, rnew, out)  # one channel fits: 1024 x 120 x 8 bytes
     ctx.sync()
     ctx.close()
+
+
+def test_other_spin_while_a_proposal_is_pending():
+    """msd_ratio on an up electron, then msd_ratio_noalloc on a down electron (which recomputes
+    the down spin's CI weights from the up table), then msd_accept of the up proposal: the state
+    and the next ratios equal those of a twin context that never made the no-allocation call."""
+    w = wl.make_workload("water", n_walkers=32)
+    p = w.problem
+    a = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    b = msd.MSD(p, w.n_walkers, "fp64", refresh_K=w.refresh_K)
+    R = torch.tensor(w.R0, device="cuda")
+    a.set_positions(R)
+    b.set_positions(R)
+    eta, u = w.proposals(3)
+    e_up, e_dn = 2, p.n_elec[0] + 1
+    rnew = torch.tensor(w.R0[:, e_up] + w.tau * eta[0], device="cuda")
+    ra, _, _ = a.ratio(e_up, rnew)
+    rb, _, _ = b.ratio(e_up, rnew)
+    dn = torch.tensor(w.R0[:, e_dn] + w.tau * eta[1], device="cuda")
+    out = [torch.empty_like(ra), torch.empty(w.n_walkers, 3, dtype=torch.float64, device="cuda"), torch.empty_like(ra)]
+    a.ratio_noalloc_into(e_dn, dn, *out)
+    acc = torch.tensor((u[0] < (ra * ra).cpu().numpy()).astype(np.uint8), device="cuda")
+    a.accept(e_up, acc)
+    b.accept(e_up, acc)
+    Ra, la, sa = a.get_state()
+    Rb, lb, sb = b.get_state()
+    assert torch.equal(Ra, Rb) and torch.equal(sa, sb)
+    assert torch.allclose(la, lb, rtol=0, atol=1e-12)
+    # the next moves (down, then up) agree as well
+    for e, t in ((e_dn, 1), (e_up, 2)):
+        Rcur = Ra.cpu().numpy()
+        rn = torch.tensor(Rcur[:, e] + w.tau * eta[t], device="cuda")
+        r1, g1, l1 = a.ratio(e, rn)
+        r2, g2, l2 = b.ratio(e, rn)
+        assert _close(r1, r2, "fp64") and _close(g1, g2, "fp64") and _close(l1, l2, "fp64")
+        acc = torch.tensor((u[t] < (r2 * r2).cpu().numpy()).astype(np.uint8), device="cuda")
+        a.accept(e, acc)
+        b.accept(e, acc)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_after_refresh_period(prec):
+    """After refresh_K moves of a spin msd_ratio starts with the from-scratch refresh and the
+    no-allocation call does not: the two then differ only by the rounding the Sherman-Morrison
+    updates accumulated since the last refresh."""
+    w = wl.make_workload("water", n_walkers=24)
+    p = w.problem
+    K = w.refresh_K
+    ctx = msd.MSD(p, w.n_walkers, prec, refresh_K=K)
+    ctx.set_positions(torch.tensor(w.R0, device="cuda"))
+    eta, u = w.proposals(K + 1)
+    R = w.R0.copy()
+    e = 1
+    for t in range(K):
+        rnew = R[:, e] + w.tau * eta[t]
+        r, _, _ = ctx.ratio(e, torch.tensor(rnew, device="cuda"))
+        acc = u[t] < (r * r).cpu().numpy()
+        ctx.accept(e, torch.tensor(acc.astype(np.uint8), device="cuda"))
+        R[acc, e] = rnew[acc]
+    rnew = torch.tensor(R[:, e] + w.tau * eta[K], device="cuda")
+    out = [torch.empty(w.n_walkers, dtype=torch.float64, device="cuda"),
+           torch.empty(w.n_walkers, 3, dtype=torch.float64, device="cuda"),
+           torch.empty(w.n_walkers, dtype=torch.float64, device="cuda")]
+    ctx.ratio_noalloc_into(e, rnew, *out)
+    r0, g0, l0 = ctx.ratio(e, rnew)  # refreshes first
+    tol = 1e-8 if prec == "fp64" else 2e-2
+    for x, y in zip(out, (r0, g0, l0)):
+        assert bool(((x - y).abs() <= tol * y.abs().clamp_min(1.0)).all()), (prec, float((x - y).abs().max()))
+    ctx.sync()
+    ctx.close()
