@@ -18,7 +18,7 @@
  *     the same table with the electron's row replaced by derivative rows);
  *   - the Sherman-Morrison update of A_0^{-1} and T on acceptance (Section III,
  *     Algorithm 1 step 1), and a from-scratch refresh every refresh_K steps
- *     (Section III: "calculated from scratch").
+ *     (Section III: the inverse and determinants recomputed directly).
  *
  * Conventions for every entry point:
  *   - Pointers named *_dev are DEVICE pointers, read and written in stream order on
@@ -220,6 +220,12 @@ msd_status msd_exc_histogram(const msd_ctx* ctx, int32_t spin, int64_t* out);
  * launches since msd_timing_start.  Any output pointer may be NULL. */
 msd_status msd_timing_start(msd_ctx* ctx);
 msd_status msd_timing_stop(msd_ctx* ctx, double* sweep_ms, int64_t* sweep_launches, int64_t* all_launches);
+/* Amortised work inside the window of the last msd_timing_start: out[0] = from-scratch refreshes
+ * of a spin (Section III: inverse and table recomputed, every refresh_K moves of that spin),
+ * out[1] = CI contractions (the weights C_s of the moving spin recomputed after the other spin
+ * changed).  Batched contexts sum over their systems.  Host-side counters; no CUDA call.
+ * MSD_ERR_ARG for a NULL argument. */
+msd_status msd_timing_counts(const msd_ctx* ctx, int64_t* out);
 
 /* Adjoint of log|Psi| at the current positions, summed over walkers with weights gbar_dev [W]:
  * dci_dev [n_det] = sum_w gbar[w] d log|Psi_w| / d c_I and dB_dev = sum_w gbar[w]
@@ -256,7 +262,10 @@ msd_status msd_set_params(msd_ctx* ctx, const double* ci_host, const double* B_u
  * in 4 MiB, else MSD_ERR_ARG; the array is shared by every context on a device, so calls that
  * overlap in time on one device race and must be serialised by the caller; the first call on
  * each device looks the array's address up (with that device current) and must come before
- * any stream capture the caller starts.  Nothing is allocated or freed by this call. */
+ * any stream capture the caller starts.  The context's device (current at msd_init) must be
+ * the current device, else MSD_ERR_ARG.  Unlike msd_ratio it never starts the periodic
+ * refresh, so after refresh_K moves of a spin it answers from the updated (not refreshed)
+ * state.  Nothing is allocated or freed by this call. */
 msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev,
                              double* grad_dev, double* lap_dev);
 

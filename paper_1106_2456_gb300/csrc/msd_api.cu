@@ -60,6 +60,7 @@ struct State {
 
 struct msd_ctx {
     int W = 0, n_tot = 0, nb = 0, K = 1;
+    int device = -1;  // the CUDA device current at msd_init (whose memory holds the context)
     bool mixed = false;
     size_t tb = 8;  // bytes of the table/orbital type
     cudaStream_t stream = nullptr;
@@ -120,6 +121,7 @@ struct msd_ctx {
     // measurement: kernel launch count and events around the excitation-sweep kernel
     bool timing = false;
     long long launches = 0;
+    long long n_refresh = 0, n_ci = 0;  // from-scratch refreshes of a spin, CI contractions (while timing)
     std::vector<cudaEvent_t> ev;  // pairs (begin, end)
     size_t ev_used = 0;
     Launch L() { return Launch{stream, d_status, timing ? &launches : nullptr}; }
@@ -496,6 +498,7 @@ msd_status refresh_spin(msd_ctx* c, State& st, int s) {
                     S.B, S.N, c->Phi);
     launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s]);
     if (S.m > 0) launch_table(c->L(), c->mixed, c->W, S.n, S.N, st.Ainv[s], c->Phi, st.T[s]);
+    if (c->timing) c->n_refresh++;
     st.since_refresh[s] = 0;
     st.C_valid[1 - s] = false;  // C of the other spin depends on this spin's t
     return check_launch(c, "refresh");
@@ -510,6 +513,7 @@ msd_status ensure_C(msd_ctx* c, State& st, int s) {
     launch_ci_contract(c->L(), c->mixed, c->W, S.g.n_exc, O.g.n_exc, S.t_off, S.t_other, S.t_c, st.t[1 - s], st.C[s]);
     launch_ci_contract_heavy(c->L(), c->mixed, c->W, S.g.n_exc, O.g.n_exc, S.n_heavy, S.heavy, S.t_off, S.t_other,
                              S.t_c, st.t[1 - s], st.C[s]);
+    if (c->timing) c->n_ci++;
     st.C_valid[s] = true;
     return check_launch(c, "CI contraction");
 }
@@ -531,8 +535,8 @@ msd_status set_positions(msd_ctx* c, State& st, const double* R_dev) {
     return rebuild(c, st);
 }
 
-// Everything from scratch at the positions in st.R (Section III: inverse and determinants
-// "calculated from scratch").
+// Everything from scratch at the positions in st.R (Section III: A_0^{-1} and every
+// determinant recomputed directly rather than updated).
 msd_status canon_refresh(msd_ctx* c, State& st, int s);
 msd_status canon_C(msd_ctx* c, State& st, int s, bool with_S);
 
@@ -870,6 +874,11 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     c->canon = p->prec == MSD_CANONICAL;
     c->tb = c->mixed ? 4 : 8;
     c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, MSD_ERR_CUDA, "no CUDA device");
+    }
     auto bail = [&](msd_status s) {
         g_init_error = c->err;
         msd_destroy(c);
@@ -1327,7 +1336,20 @@ msd_status msd_timing_start(msd_ctx* c) {
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
     c->timing = true;
     c->launches = 0;
+    c->n_refresh = 0;
+    c->n_ci = 0;
     c->ev_used = 0;
+    return MSD_OK;
+}
+
+msd_status msd_timing_counts(const msd_ctx* c, int64_t* out) {
+    if (!c || !out) return MSD_ERR_ARG;
+    out[0] = c->n_refresh;
+    out[1] = c->n_ci;
+    for (const msd_ctx* sc : c->sub) {
+        out[0] += sc->n_refresh;
+        out[1] += sc->n_ci;
+    }
     return MSD_OK;
 }
 
@@ -1494,8 +1516,15 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
                     "msd_ratio_noalloc needs %zu bytes of scratch (walkers x channels x orbitals x %d bytes), "
                     "above its fixed limit of %zu bytes; use msd_ratio",
                     need, c->tb, kNoAllocScratchBytes);
+    // the scratch array is looked up for the current device: it must be the context's own
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev != c->device)
+        return fail(c, MSD_ERR_ARG, "msd_ratio_noalloc: current device %d is not the context's device %d", dev,
+                    c->device);
     void* phi = nullptr;
-    cudaError_t e = noalloc_scratch(&phi);
+    e = noalloc_scratch(&phi);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
     TRY(ensure_C(c, st, s));
     launch_orbitals(c->L(), c->mixed, nch, c->W, 1, rnew_dev, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, phi);

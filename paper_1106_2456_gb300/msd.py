@@ -107,6 +107,7 @@ def load_library():
         "msd_copy_state": ([vp, i32, i32, vp, vp], i32),
         "msd_timing_start": ([vp], i32),
         "msd_timing_stop": ([vp, vp, vp, vp], i32),
+        "msd_timing_counts": ([vp, vp], i32),
         "msd_set_hamiltonian": ([vp, vp, vp], i32),
         "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
         "msd_local_energy": ([vp, vp, vp], i32),
@@ -384,6 +385,12 @@ class MSD:
         self._check(self.lib.msd_timing_stop(self.ctx, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
         return ms.value, n1.value, n2.value
 
+    def timing_counts(self):
+        """(from-scratch refreshes of a spin, CI contractions) since timing_start."""
+        out = np.zeros(2, dtype=np.int64)
+        self._check(self.lib.msd_timing_counts(self.ctx, out.ctypes.data))
+        return int(out[0]), int(out[1])
+
     def exc_histogram(self, spin: int) -> np.ndarray:
         out = np.zeros(1 + 9, dtype=np.int64)
         self._check(self.lib.msd_exc_histogram(self.ctx, int(spin), out.ctypes.data))
@@ -497,3 +504,8 @@ class MSDBatch:
         ms, n1, n2 = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.msd_timing_stop(self.ctx, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
         return ms.value, n1.value, n2.value
+
+    def timing_counts(self):
+        out = np.zeros(2, dtype=np.int64)
+        self._check(self.lib.msd_timing_counts(self.ctx, out.ctypes.data))
+        return int(out[0]), int(out[1])
