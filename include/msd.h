@@ -269,6 +269,15 @@ msd_status msd_set_params(msd_ctx* ctx, const double* ci_host, const double* B_u
 msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev, double* ratio_dev,
                              double* grad_dev, double* lap_dev);
 
+/* Orbitals of spin `spin` at n_points positions pos_dev [n_points][3] (Algorithm 1 step 2):
+ * out_dev [n_points][nch][n_orb[spin]] = phi_j and, for nch = 5, its gradient and laplacian,
+ * d^a phi_j(r) = sum_mu d^a chi_mu(r) B[mu][j], in the context's orbital precision (FP64 in
+ * MSD_FP64; FP32 in MSD_MIXED, where the contraction runs on the tensor cores with FP32 accuracy:
+ * three TF32 pieces per operand).  The same evaluation the library runs at proposals and refreshes.
+ * No state changes.  MSD_ERR_ARG for nch not 1 or 5, a batched context or the canonical method. */
+msd_status msd_orbitals(msd_ctx* ctx, int32_t spin, int32_t nch, int32_t n_points, const double* pos_dev,
+                        void* out_dev);
+
 /*
  * VMC energy driver.  The paper runs VMC on Psi_T = exp(J) Psi_MD (Section VI) and leaves the
  * Jastrow factor J to standard methods (Section II); these calls supply a simple one and the

@@ -25,6 +25,8 @@ thread_local std::string g_init_error;
 struct SpinConst {
     int n = 0, N = 0, m = 0, off = 0;
     void* B = nullptr;            // [nb][N] (double or float)
+    float* Bsplit = nullptr;      // FP32 path: B in three TF32 pieces for the tensor-core orbitals
+    TcPlan tc;
     ExcDev g;                     // device strings, grouped by order
     std::vector<int> user_of;     // internal index -> user index
     std::vector<int> internal_of; // user index -> internal index
@@ -65,6 +67,7 @@ struct msd_ctx {
     size_t tb = 8;  // bytes of the table/orbital type
     cudaStream_t stream = nullptr;
     double4* bas = nullptr;
+    float4* basf = nullptr;    // FP32 path: centres as (hi, lo) float pairs and exponents (tensor-core orbitals)
     int8_t* blm = nullptr;
     SpinConst sp[2];
     State st, scratch;
@@ -90,8 +93,7 @@ struct msd_ctx {
     double* cn_Phi[2] = {nullptr, nullptr};  // [W][n][N] orbitals of the current positions
     uint8_t* cn_used[2] = {nullptr, nullptr};
     // all-electron gradient/laplacian workspace (allocated on first use)
-    double* ga_G = nullptr;    // [W][n_max][m_max]
-    double* ga_U = nullptr;    // [W][n_max][n_max]
+    void* ga_G = nullptr;      // [W][n_max][m_max] (table precision)
     void* ga_phid = nullptr;   // [W n_max][5][N_max]
     // msd_backward: internal strings of every term, and workspace allocated on first use
     long long n_det = 0;
@@ -491,11 +493,31 @@ msd_status alloc_state(msd_ctx* c, State& st) {
     return MSD_OK;
 }
 
+// Orbitals of spin s at P points (Algorithm 1 step 2): on the tensor cores for the FP32 path,
+// by the SIMT product in FP64.
+void orbitals(msd_ctx* c, const SpinConst& S, int nch, int P, int ppw, const double* pos, long long wstride,
+              int p_off, void* out) {
+    if (c->mixed && S.Bsplit)
+        launch_orbitals_tc(c->L(), nch, P, ppw, pos, wstride, p_off, c->basf, c->blm, c->nb, S.tc, S.Bsplit, S.N,
+                           static_cast<float*>(out));
+    else
+        launch_orbitals(c->L(), c->mixed, nch, P, ppw, pos, wstride, p_off, c->bas, c->blm, c->nb, S.B, S.N, out);
+}
+
+// The three TF32 pieces of B_s (from its FP64 value) for the tensor-core orbitals.
+msd_status upload_split_B(msd_ctx* c, SpinConst& S, const double* B_host) {
+    std::vector<float> h(S.tc.floats);
+    tc_split_B(S.tc, c->nb, S.N, B_host, h.data());
+    if (!S.Bsplit) TRY(dalloc(c, &S.Bsplit, h.size()));
+    const cudaError_t e = cudaMemcpy(S.Bsplit, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "upload of the split B: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
 // A7: recompute A_0^{-1}, log|det A_0| and T of spin s from the positions (Section III).
 msd_status refresh_spin(msd_ctx* c, State& st, int s) {
     const SpinConst& S = c->sp[s];
-    launch_orbitals(c->L(), c->mixed, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas, c->blm, c->nb,
-                    S.B, S.N, c->Phi);
+    orbitals(c, S, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->Phi);
     launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s]);
     if (S.m > 0) launch_table(c->L(), c->mixed, c->W, S.n, S.N, st.Ainv[s], c->Phi, st.T[s]);
     if (c->timing) c->n_refresh++;
@@ -593,8 +615,7 @@ msd_status grad_lap_one(msd_ctx* c, State& st, int e, double* grad, long long gs
     const int s = spin_of(c, e);
     const SpinConst& S = c->sp[s];
     TRY(ensure_C(c, st, s));
-    launch_orbitals(c->L(), c->mixed, NCH, c->W, 1, st.R, (long long)c->n_tot * 3, e, c->bas, c->blm, c->nb, S.B, S.N,
-                    c->phi_tmp);
+    orbitals(c, S, NCH, c->W, 1, st.R, (long long)c->n_tot * 3, e, c->phi_tmp);
     RatioArgs a{};
     a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = e - S.off; a.nch = NCH;
     a.phi = c->phi_tmp; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
@@ -658,8 +679,9 @@ int sub_elec(const msd_ctx* c, int s, int elec) { return elec % c->sub[s]->n_tot
 msd_status build_batch_plan(msd_ctx* c) {
     const int ns = (int)c->sub.size();
     std::vector<BatchSys> sys(ns);
-    std::vector<int4> tiles;
+    std::vector<int4> tiles, tc_tiles;
     std::vector<int> wsys;
+    size_t tc_smem = 0;
     std::vector<size_t> sys_smem(ns, 0);
     size_t rsm = 0, asm_ = 0;
     const int TP = orbital_tile_points(), TJ = orbital_tile_orbitals();
@@ -672,10 +694,12 @@ msd_status build_batch_plan(msd_ctx* c) {
         B.w_off = (int)c->w_off[q];
         B.status = sc->d_status;
         B.R = sc->st.R;
-        int Nmax = 0;
+        int Nmax = 0, nT = 0;
         for (int s = 0; s < 2; ++s) {
             const SpinConst& S = sc->sp[s];
-            B.orb[s] = OrbArgs{sc->bas, sc->blm, sc->nb, S.B, S.N, sc->phi_new};
+            B.orb[s] = OrbArgs{sc->bas, sc->blm, sc->nb, S.B, S.N, sc->phi_new, S.Bsplit, S.tc.TN, S.tc.nT, sc->basf};
+            if (S.Bsplit) tc_smem = std::max(tc_smem, S.tc.smem);
+            nT = std::max(nT, S.tc.nT);
             RatioArgs& a = B.ratio[s];
             a = RatioArgs{};
             a.W = sc->W; a.n = S.n; a.N = S.N; a.m = S.m;
@@ -697,6 +721,11 @@ msd_status build_batch_plan(msd_ctx* c) {
         for (int w = 0; w < sc->W; ++w) wsys.push_back(q);
         for (int p0 = 0; p0 < sc->W; p0 += TP)
             for (int j0 = 0; j0 < Nmax; j0 += TJ) tiles.push_back(make_int4(q, p0, j0, 0));
+        if (c->mixed) {
+            const int ppt = tc_tile_points(NCH);  // the five-channel tiling covers the one-channel one
+            for (int x = 0; x * ppt < sc->W; ++x)
+                for (int y = 0; y < nT; ++y) tc_tiles.push_back(make_int4(q, x, y, 0));
+        }
     }
     // ratio blocks grouped by shared-memory size class (the CTAs an SM can hold), largest last
     auto cls = [&](size_t sm) {
@@ -728,6 +757,13 @@ msd_status build_batch_plan(msd_ctx* c) {
     TRY(upload(c, &d_sys, sys.data(), sys.size()));
     TRY(upload(c, &d_blk, blk.data(), blk.size()));
     TRY(upload(c, &d_tiles, tiles.data(), tiles.size()));
+    if (!tc_tiles.empty()) {
+        int4* d_tc = nullptr;
+        TRY(upload(c, &d_tc, tc_tiles.data(), tc_tiles.size()));
+        c->bplan.tc_tiles = d_tc;
+        c->bplan.n_tc_tiles = (int)tc_tiles.size();
+        c->bplan.tc_smem = tc_smem;
+    }
     TRY(upload(c, &d_wsys, wsys.data(), wsys.size()));
     TRY(dalloc(c, &c->b_rnew, (size_t)c->W * 3));
     c->bplan.sys = d_sys;
@@ -784,7 +820,10 @@ msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* rat
     const cudaError_t e = cudaMemcpyAsync(c->b_rnew, rnew_dev, sizeof(double) * 3 * c->W, cudaMemcpyDeviceToDevice,
                                           c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
-    launch_orbitals_batched(c->L(), c->mixed, c->bplan, elec, nch, c->b_rnew);
+    if (c->mixed && c->bplan.n_tc_tiles > 0)
+        launch_orbitals_tc_batched(c->L(), c->bplan, elec, nch, c->b_rnew);
+    else
+        launch_orbitals_batched(c->L(), c->mixed, c->bplan, elec, nch, c->b_rnew);
     launch_ratio_batched(c->L_sweep(), c->mixed, c->bplan, elec, nch, ratio_dev, grad_dev, lap_dev);
     return check_launch(c, "batched ratio");
 }
@@ -897,6 +936,14 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
         bas[mu] = make_double4(A[0], A[1], A[2], p->bas_alpha[mu]);
     }
     if ((st = upload(c, &c->bas, bas.data(), bas.size())) != MSD_OK) return bail(st);
+    if (c->mixed) {
+        std::vector<double> cen(3 * (size_t)c->nb);
+        for (int mu = 0; mu < c->nb; ++mu)
+            for (int i = 0; i < 3; ++i) cen[3 * mu + i] = p->nuc_xyz[3 * p->bas_center[mu] + i];
+        std::vector<float4> bf(2 * (size_t)c->nb);
+        tc_basis_pairs(c->nb, cen.data(), p->bas_alpha, reinterpret_cast<float*>(bf.data()));
+        if ((st = upload(c, &c->basf, bf.data(), bf.size())) != MSD_OK) return bail(st);
+    }
     if ((st = upload(c, &c->blm, p->bas_lm, (size_t)c->nb)) != MSD_OK) return bail(st);
     for (int s = 0; s < 2; ++s) {
         SpinConst& S = c->sp[s];
@@ -906,6 +953,8 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
             float* d = nullptr;
             if ((st = upload(c, &d, b32.data(), cnt)) != MSD_OK) return bail(st);
             S.B = d;
+            S.tc = tc_plan(c->nb, S.N);
+            if ((st = upload_split_B(c, S, p->B[s])) != MSD_OK) return bail(st);
         } else {
             double* d = nullptr;
             if ((st = upload(c, &d, p->B[s], cnt)) != MSD_OK) return bail(st);
@@ -1046,7 +1095,7 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
     const int nch = grad_dev ? NCH : 1;
     cudaError_t e = cudaMemcpyAsync(c->rnew, rnew_dev, sizeof(double) * c->W * 3, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
-    launch_orbitals(c->L(), c->mixed, nch, c->W, 1, c->rnew, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, c->phi_new);
+    orbitals(c, S, nch, c->W, 1, c->rnew, 3, 0, c->phi_new);
     RatioArgs a{};
     a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = elec - S.off; a.nch = nch;
     a.phi = c->phi_new; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
@@ -1113,8 +1162,7 @@ msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_
         const int Nmax = std::max(c->sp[0].N, c->sp[1].N);
         const int mmax = std::max(1, std::max(c->sp[0].m, c->sp[1].m));
         if (!c->bw_M) TRY(dalloc(c, &c->bw_M, W * nmax * Nmax));
-        if (!c->ga_G) TRY(dalloc(c, &c->ga_G, W * nmax * mmax));
-        if (!c->ga_U) TRY(dalloc(c, &c->ga_U, W * nmax * nmax));
+        if (!c->ga_G) TRY(valloc(c, &c->ga_G, W * nmax * mmax * c->tb));
         if (!c->ga_phid) TRY(valloc(c, &c->ga_phid, W * nmax * NCH * Nmax * c->tb));
         for (int s = 0; s < 2; ++s) {
             const SpinConst& S = c->sp[s];
@@ -1126,10 +1174,9 @@ msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_
             }
             TRY(ensure_C(c, st, s));
             launch_tbar(c->L(), c->mixed, c->W, S.n, S.m, S.N, S.g, st.T[s], st.C[s], st.S, c->bw_M);
-            launch_orbitals(c->L(), c->mixed, NCH, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->bas,
-                            c->blm, c->nb, S.B, S.N, c->ga_phid);
+            orbitals(c, S, NCH, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->ga_phid);
             launch_all_gradlap(c->L(), c->mixed, c->W, S.n, S.m, S.N, c->n_tot, S.off, st.Ainv[s], st.T[s], c->bw_M,
-                               c->ga_phid, c->ga_G, c->ga_U, grad_dev, lap_dev);
+                               c->ga_phid, c->ga_G, grad_dev, lap_dev);
             TRY(check_launch(c, "all-electron gradient"));
         }
     }
@@ -1274,6 +1321,8 @@ msd_status msd_sync(msd_ctx* c) {
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "status read: %s", cudaGetErrorString(e));
     if (status) {
         cudaMemset(c->d_status, 0, sizeof(int));
+        if (status & ST_TIMEOUT)
+            return fail(c, MSD_ERR_TIMEOUT, "a bounded wait of a tensor-core kernel gave up (result not written)");
         if (status & ST_SINGULAR) return fail(c, MSD_ERR_SINGULAR, "a reference determinant or ratio was zero");
         return fail(c, MSD_ERR_SINGULAR, "a ratio was not finite");
     }
@@ -1527,7 +1576,7 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
     e = noalloc_scratch(&phi);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
     TRY(ensure_C(c, st, s));
-    launch_orbitals(c->L(), c->mixed, nch, c->W, 1, rnew_dev, 3, 0, c->bas, c->blm, c->nb, S.B, S.N, phi);
+    orbitals(c, S, nch, c->W, 1, rnew_dev, 3, 0, phi);
     RatioArgs a{};
     a.W = c->W; a.n = S.n; a.N = S.N; a.m = S.m; a.row = elec - S.off; a.nch = nch;
     a.phi = phi; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.C = st.C[s]; a.S = st.S; a.g = S.g;
@@ -1536,6 +1585,18 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
     if (S.m == 0) a.g.kmax = 0;
     launch_ratio(c->L(), c->mixed, a);
     return check_launch(c, "ratio (no allocation)");
+}
+
+msd_status msd_orbitals(msd_ctx* c, int32_t spin, int32_t nch, int32_t n_points, const double* pos_dev,
+                        void* out_dev) {
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_orbitals takes a single-system context");
+    if (!c || !pos_dev || !out_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (spin < 0 || spin > 1) return fail(c, MSD_ERR_ARG, "spin %d is not 0 or 1", spin);
+    if (nch != 1 && nch != NCH) return fail(c, MSD_ERR_ARG, "nch = %d must be 1 or 5", nch);
+    if (n_points < 0) return fail(c, MSD_ERR_ARG, "n_points = %d < 0", n_points);
+    if (c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
+    orbitals(c, c->sp[spin], nch, n_points, 1, pos_dev, 3, 0, out_dev);
+    return check_launch(c, "orbitals");
 }
 
 msd_status msd_backward(msd_ctx* c, const double* gbar_dev, double* dci_dev, double* dB_dev) {
@@ -1617,6 +1678,10 @@ msd_status msd_set_params(msd_ctx* c, const double* ci_host, const double* B_up_
             if (c->mixed) {
                 std::vector<float> b32(Bh, Bh + cnt);
                 e = cudaMemcpy(S.B, b32.data(), sizeof(float) * cnt, cudaMemcpyHostToDevice);
+                if (e == cudaSuccess && S.Bsplit) {
+                    const msd_status r = upload_split_B(c, S, Bh);
+                    if (r != MSD_OK) return r;
+                }
             } else {
                 e = cudaMemcpy(S.B, Bh, sizeof(double) * cnt, cudaMemcpyHostToDevice);
             }

@@ -253,48 +253,155 @@ __global__ void __launch_bounds__(kBB) k_dB(int P, int nb, int N, int pchunk, co
 //   d^a Psi / Psi for electron i = s^a(i) + sum_p y^a_i[p] G'[i][p],
 //   s^a(i) = d^a phi_occ(r_i) . A_0^{-1}[:, i],  y^a_i = d^a phi_virt(r_i) - T^T d^a phi_occ(r_i),
 //   G'[i][p] = sum_h A_0^{-1}[h][i] Tbar[h][p]  (the G of a move of electron i, divided by S).
-// One block per walker; G' and U = T G'^T in global scratch.
-template <typename TO, typename TT>
+// With U = T G'^T (n x n) this is
+//   num^a[i] = sum_c d^a phi_occ(r_i)[c] (A_0^{-1} - U)[c][i] + sum_p d^a phi_virt(r_i)[p] G'[i][p].
+// One block per walker, two tiled products in shared memory: G' = A_0^{-T} Tbar in 64 x 64 output
+// tiles (written to global scratch), then U in 64 x 64 tiles, each turned into V = A_0^{-1} - U
+// and contracted with the occupied orbital derivatives at once.  Every thread owns a 4 x 4
+// register tile; products run in TC (FP32 on the mixed path, whose table is FP32, FP64 otherwise).
+constexpr int kGT = 64;       // output tile edge
+constexpr int kGK = 32;       // depth of one staged slab
+constexpr int kGLd = kGT + 4; // row stride of the staged tiles (16-byte aligned rows)
+
+template <typename TC>
+__host__ __device__ constexpr size_t gradlap_smem_bytes() {
+    return sizeof(TC) * (2 * (size_t)kGK * kGLd + (size_t)kGT * kGLd) + sizeof(double) * 4 * 256;
+}
+
+template <typename TO, typename TT, typename TC>
 __global__ void __launch_bounds__(kBB) k_all_gradlap(int n, int m, int N, int n_tot, int e_off,
                                                     const double* __restrict__ Ainv, const TT* __restrict__ T,
                                                     const double* __restrict__ M, const TO* __restrict__ phid,
-                                                    double* __restrict__ Gp, double* __restrict__ U,
-                                                    double* __restrict__ grad, double* __restrict__ lap) {
-    const int w = blockIdx.x;
-    const double* Aw = Ainv + (long long)w * n * n;
+                                                    TC* __restrict__ Gp, double* __restrict__ grad,
+                                                    double* __restrict__ lap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TC* Xs = reinterpret_cast<TC*>(smem);          // [kGK][kGLd] left slab, [k][row]
+    TC* Ys = Xs + kGK * kGLd;                       // [kGK][kGLd] right slab, [k][col]
+    TC* Vs = Ys + kGK * kGLd;                       // [kGT][kGLd] V tile, [c][i]
+    double* nums = reinterpret_cast<double*>(Vs + kGT * kGLd);  // [4][256] per-electron sums (n <= 256)
+    const int w = blockIdx.x, tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;         // output rows 4 ty .. 4 ty + 3, cols 4 tx .. 4 tx + 3
+    const double* Aw = Ainv + (long long)w * n * n;  // A_0^{-1}[c][r] at Aw[c n + r]
     const TT* Tw = T + (long long)w * n * m;
-    const double* Mw = M + (long long)w * n * N;  // Tbar[h][p] at Mw[h * N + n + p]
-    double* Gw = Gp + (long long)w * n * m;
-    double* Uw = U + (long long)w * n * n;
-    for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
-        const int i = idx / m, p = idx - i * m;
-        double acc = 0.0;
-        for (int h = 0; h < n; ++h) acc = fma(Aw[(long long)h * n + i], Mw[(long long)h * N + n + p], acc);
-        Gw[idx] = acc;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int c = idx / n, i = idx - c * n;
-        double acc = 0.0;
-        for (int p = 0; p < m; ++p) acc = fma(double(Tw[(long long)c * m + p]), Gw[(long long)i * m + p], acc);
-        Uw[idx] = acc;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const TO* ph = phid + ((long long)w * n + i) * 5 * N;
-        double num[5];
+    const double* Mw = M + (long long)w * n * N;    // Tbar[h][p] at Mw[h N + n + p]
+    TC* Gw = Gp + (long long)w * n * m;
+    const TO* phw = phid + (long long)w * n * 5 * N;  // d^a phi(r_i)[j] at phw[(i 5 + a) N + j]
+    for (int q = tid; q < 4 * 256; q += kBB) nums[q] = 0.0;
+
+    // G'[i][p] = sum_h A[h][i] Tbar[h][p]: left slab Xs[k][i] = A[h0 + k][i0 + i], right Ys[k][p] = Tbar
+    for (int i0 = 0; i0 < n; i0 += kGT)
+        for (int p0 = 0; p0 < m; p0 += kGT) {
+            TC acc[4][4];
 #pragma unroll
-        for (int a = 1; a < 5; ++a) {
-            const TO* pa = ph + a * N;
-            double v = 0.0;
-            for (int c = 0; c < n; ++c)
-                v = fma(double(pa[c]), Aw[(long long)c * n + i] - Uw[(long long)c * n + i], v);
-            for (int p = 0; p < m; ++p) v = fma(double(pa[n + p]), Gw[(long long)i * m + p], v);
-            num[a] = v;
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
+            for (int h0 = 0; h0 < n; h0 += kGK) {
+                __syncthreads();
+                for (int q = tid; q < kGK * kGT; q += kBB) {
+                    const int k = q / kGT, j = q - k * kGT, h = h0 + k;
+                    Xs[k * kGLd + j] = (h < n && i0 + j < n) ? TC(Aw[(long long)h * n + i0 + j]) : TC(0);
+                    Ys[k * kGLd + j] = (h < n && p0 + j < m) ? TC(Mw[(long long)h * N + n + p0 + j]) : TC(0);
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int k = 0; k < kGK; ++k) {
+                    TC xa[4], yb[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xa[a] = Xs[k * kGLd + 4 * ty + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) yb[b] = Ys[k * kGLd + 4 * tx + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int i = i0 + 4 * ty + a;
+                if (i >= n) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int p = p0 + 4 * tx + b;
+                    if (p < m) Gw[(long long)i * m + p] = acc[a][b];
+                }
+            }
         }
+    __syncthreads();  // G' of this walker complete (block-wide visibility of its global writes)
+
+    // U[c][i] = sum_p T[c][p] G'[i][p] per 64 x 64 tile; V = A - U; num^a[i] += sum_c dphi^a[i][c] V[c][i]
+    for (int i0 = 0; i0 < n; i0 += kGT)
+        for (int c0 = 0; c0 < n; c0 += kGT) {
+            TC acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
+            for (int q0 = 0; q0 < m; q0 += kGK) {
+                __syncthreads();
+                for (int q = tid; q < kGK * kGT; q += kBB) {
+                    // consecutive threads read consecutive p of one row (coalesced), stored [p][row]
+                    const int j = q / kGK, k = q - j * kGK, pp = q0 + k;
+                    Xs[k * kGLd + j] = (pp < m && c0 + j < n) ? TC(Tw[(long long)(c0 + j) * m + pp]) : TC(0);
+                    Ys[k * kGLd + j] = (pp < m && i0 + j < n) ? Gw[(long long)(i0 + j) * m + pp] : TC(0);
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int k = 0; k < kGK; ++k) {
+                    TC xa[4], yb[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xa[a] = Xs[k * kGLd + 4 * ty + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) yb[b] = Ys[k * kGLd + 4 * tx + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+                }
+            }
+            // V tile [c][i] = A[c][i] - U[c][i]
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int c = c0 + 4 * ty + a;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int i = i0 + 4 * tx + b;
+                    Vs[(4 * ty + a) * kGLd + 4 * tx + b] =
+                        (c < n && i < n) ? TC(Aw[(long long)c * n + i]) - acc[a][b] : TC(0);
+                }
+            }
+            __syncthreads();
+            // thread (electron i0 + ii, channel 1 + ch): sum over this tile's occupied orbitals c
+            {
+                const int ii = tid & 63, ch = tid >> 6, i = i0 + ii;
+                if (i < n) {
+                    const TO* pa = phw + ((long long)i * 5 + 1 + ch) * N + c0;
+                    TC v = TC(0);
+                    const int cn = min(kGT, n - c0);
+                    for (int cc = 0; cc < cn; ++cc) v = fma(TC(pa[cc]), Vs[cc * kGLd + ii], v);
+                    nums[ch * 256 + i] += double(v);
+                }
+            }
+        }
+    __syncthreads();
+    // the virtual part: num^a[i] += sum_p d^a phi_virt(r_i)[p] G'[i][p], one warp per (electron, channel)
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int q = warp; q < 4 * n; q += kBB / 32) {
+        const int i = q >> 2, ch = q & 3;
+        const TO* pa = phw + ((long long)i * 5 + 1 + ch) * N + n;
+        const TC* gi = Gw + (long long)i * m;
+        TC v = TC(0);
+        for (int p = lane; p < m; p += 32) v = fma(TC(pa[p]), gi[p], v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) nums[ch * 256 + i] += double(v);
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += kBB) {
         const long long e = (long long)w * n_tot + e_off + i;
-        for (int d = 0; d < 3; ++d) grad[e * 3 + d] = num[1 + d];
-        lap[e] = num[4];
+        for (int d = 0; d < 3; ++d) grad[e * 3 + d] = nums[d * 256 + i];
+        lap[e] = nums[3 * 256 + i];
     }
 }
 
@@ -379,15 +486,25 @@ void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const 
 }
 
 void launch_all_gradlap(const Launch& L, bool mixed, int W, int n, int m, int N, int n_tot, int e_off,
-                        const double* Ainv, const void* T, const double* M, const void* phid, double* Gp, double* U,
-                        double* grad, double* lap) {
+                        const double* Ainv, const void* T, const double* M, const void* phid, void* Gp, double* grad,
+                        double* lap) {
     L.count();
-    if (mixed)
-        k_all_gradlap<float, float><<<W, kBB, 0, L.stream>>>(n, m, N, n_tot, e_off, Ainv, static_cast<const float*>(T), M,
-                                                           static_cast<const float*>(phid), Gp, U, grad, lap);
-    else
-        k_all_gradlap<double, double><<<W, kBB, 0, L.stream>>>(n, m, N, n_tot, e_off, Ainv, static_cast<const double*>(T),
-                                                             M, static_cast<const double*>(phid), Gp, U, grad, lap);
+    if (mixed) {
+        const size_t sm = gradlap_smem_bytes<float>();
+        cudaFuncSetAttribute(k_all_gradlap<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_all_gradlap<float, float, float><<<W, kBB, sm, L.stream>>>(n, m, N, n_tot, e_off, Ainv,
+                                                                   static_cast<const float*>(T), M,
+                                                                   static_cast<const float*>(phid),
+                                                                   static_cast<float*>(Gp), grad, lap);
+    } else {
+        const size_t sm = gradlap_smem_bytes<double>();
+        cudaFuncSetAttribute(k_all_gradlap<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+        k_all_gradlap<double, double, double><<<W, kBB, sm, L.stream>>>(n, m, N, n_tot, e_off, Ainv,
+                                                                      static_cast<const double*>(T), M,
+                                                                      static_cast<const double*>(phid),
+                                                                      static_cast<double*>(Gp), grad, lap);
+    }
 }
 
 }  // namespace msd

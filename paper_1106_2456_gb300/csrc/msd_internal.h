@@ -14,7 +14,7 @@ namespace msd {
 constexpr int MAXK = MSD_MAX_ORDER;
 constexpr int NCH = 5;  // channels: value, d/dx, d/dy, d/dz, laplacian
 
-enum StatusBits : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
+enum StatusBits : int { ST_SINGULAR = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 
 // Bytes of one excitation record of order k: k hole bytes, k particle bytes, padded to a
 // power of two so one vector load fetches it.
@@ -59,6 +59,22 @@ struct Launch {
 void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const double* pos,
                      long long wstride, int p_off, const double4* bas, const int8_t* blm, int nb,
                      const void* B, int N, void* out);
+
+// The same orbitals on the tensor cores (FP32 path, msd_orbitals_tc.cu): B of one spin split on
+// the host into three TF32 pieces in the operand layout the kernel copies (tc_split_B), TN <= 256
+// columns per tile, nT column tiles, nK chunks of 8 basis functions; out is FP32.
+struct TcPlan {
+    int nT = 0, TN = 0, nK = 0;
+    size_t floats = 0;  // size of the split B
+    size_t smem = 0;    // dynamic shared memory per block
+};
+TcPlan tc_plan(int nb, int N);
+void tc_split_B(const TcPlan& t, int nb, int N, const double* B, float* out);
+// basf [nb][2] float4: (centre hi, alpha), (centre lo, 0) from centres [nb][3] and exponents [nb].
+void tc_basis_pairs(int nb, const double* centers, const double* alpha, float* out);
+void launch_orbitals_tc(const Launch& L, int nch, int P, int ppw, const double* pos, long long wstride, int p_off,
+                        const float4* basf, const int8_t* blm, int nb, const TcPlan& t, const float* Bsplit, int N,
+                        float* out);
 
 // Gauss-Jordan inverse with partial pivoting of A_0 = Phi[w][:, :n] for every walker.
 void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv,
@@ -136,6 +152,9 @@ struct OrbArgs {
     const void* B;   // [nb][N] of the spin
     int N;
     void* out;       // [W][nch][N] orbitals at the proposed positions
+    const float* Bsplit;  // FP32 path: B in TF32 pieces for the tensor cores (TcPlan of the spin)
+    int TN, nT;
+    const float4* basf;   // FP32 path: basis centres as (hi, lo) pairs (tc_basis_pairs)
 };
 struct BatchSys {
     int n_tot, n_up, W, w_off;  // electrons, walkers, offset of the walkers in concatenated arrays
@@ -160,8 +179,15 @@ struct BatchPlan {
     int n_tiles = 0;
     const int* wsys = nullptr;  // system of each concatenated walker
     size_t ratio_smem = 0, accept_smem = 0;
+    // FP32 path: tensor-core orbital tiles (system, point tile of 25, column tile, -) and their
+    // shared memory (the largest any system needs)
+    const int4* tc_tiles = nullptr;
+    int n_tc_tiles = 0;
+    size_t tc_smem = 0;
 };
 void launch_orbitals_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const double* rnew);
+void launch_orbitals_tc_batched(const Launch& L, const BatchPlan& P, int t, int nch, const double* rnew);
+int tc_tile_points(int nch);  // points per tensor-core tile for 1 or 5 channels
 void launch_ratio_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, double* ratio, double* grad,
                           double* lap);
 void launch_accept_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const uint8_t* accept,
@@ -197,9 +223,10 @@ void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const 
                  const double* S, double* M);
 // grad [W][n_tot][3] and lap [W][n_tot] of the spin's electrons e_off .. e_off + n - 1 from Tbar
 // (in M) and the orbitals with derivatives at every electron, phid [W n][5][N].
+// G' = A_0^{-T} Tbar goes to Gp [W][n][m] (FP32 on the mixed path, FP64 otherwise); n <= 256.
 void launch_all_gradlap(const Launch& L, bool mixed, int W, int n, int m, int N, int n_tot, int e_off,
-                        const double* Ainv, const void* T, const double* M, const void* phid, double* Gp, double* U,
-                        double* grad, double* lap);
+                        const double* Ainv, const void* T, const double* M, const void* phid, void* Gp, double* grad,
+                        double* lap);
 // chi[p][mu] (values, FP64) at P points laid out as for launch_orbitals.
 void launch_chi(const Launch& L, int P, int ppw, const double* pos, long long wstride, int p_off, const double4* bas,
                 const int8_t* blm, int nb, double* chi);

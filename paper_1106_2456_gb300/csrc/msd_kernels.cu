@@ -19,6 +19,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "msd_basis.cuh"
 #include "msd_internal.h"
 #include "msd_records.cuh"
 #include "msd_smalldet.cuh"
@@ -27,9 +28,6 @@ namespace msd {
 namespace {
 
 constexpr int kBlock = 256;
-
-__device__ __forceinline__ float texp(float x) { return expf(x); }
-__device__ __forceinline__ double texp(double x) { return exp(x); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -89,28 +87,6 @@ __device__ __forceinline__ void copy_to_smem(TT* dst, const TT* __restrict__ src
 constexpr int kOrbTP = MSD_ORB_TP;   // points per tile (16 threads per point group)
 constexpr int kOrbPPT = kOrbTP / 16;  // points per thread
 constexpr int kOrbTJ = 64;
-
-template <typename TO>
-__device__ __forceinline__ void basis_channels(const double* rp, double4 b, int lm, TO (&v)[5]) {
-    const TO d[3] = {TO(rp[0] - b.x), TO(rp[1] - b.y), TO(rp[2] - b.z)};
-    const TO al = TO(b.w);
-    const TO d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const TO g = texp(-al * d2);
-    if (lm == 0) {
-        v[0] = g;
-        v[1] = TO(-2) * al * d[0] * g;
-        v[2] = TO(-2) * al * d[1] * g;
-        v[3] = TO(-2) * al * d[2] * g;
-        v[4] = (TO(4) * al * al * d2 - TO(6) * al) * g;
-    } else {
-        const int c = lm - 1;
-        const TO dc = d[c];
-        v[0] = dc * g;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) v[1 + a] = ((a == c ? TO(1) : TO(0)) - TO(2) * al * d[a] * dc) * g;
-        v[4] = dc * (TO(4) * al * al * d2 - TO(10) * al) * g;
-    }
-}
 
 template <typename TO>
 constexpr int orb_kc() {

@@ -108,6 +108,7 @@ def load_library():
         "msd_timing_start": ([vp], i32),
         "msd_timing_stop": ([vp, vp, vp, vp], i32),
         "msd_timing_counts": ([vp, vp], i32),
+        "msd_orbitals": ([vp, i32, i32, i32, vp, vp], i32),
         "msd_set_hamiltonian": ([vp, vp, vp], i32),
         "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
         "msd_local_energy": ([vp, vp, vp], i32),
@@ -384,6 +385,15 @@ class MSD:
         n2 = ctypes.c_int64()
         self._check(self.lib.msd_timing_stop(self.ctx, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
         return ms.value, n1.value, n2.value
+
+    def orbitals(self, spin: int, pos: torch.Tensor, nch: int = 5) -> torch.Tensor:
+        """msd_orbitals: [P][nch][N] orbitals (and derivatives) of one spin at pos [P][3]."""
+        P = int(pos.shape[0])
+        N = int(self.p.n_orb[spin])
+        out = torch.empty(P, nch, N, dtype=torch.float32 if self.mixed else torch.float64, device=self.dev)
+        self._check(self.lib.msd_orbitals(self.ctx, int(spin), int(nch), P, _dptr(pos, torch.float64, (P, 3), "pos"),
+                                          out.data_ptr()))
+        return out
 
     def timing_counts(self):
         """(from-scratch refreshes of a spin, CI contractions) since timing_start."""

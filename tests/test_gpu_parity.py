@@ -5,7 +5,7 @@ Every ratio, gradient component and laplacian X is compared as
 largest condition number of the reference Slater matrices involved in the move:
 FP64: tol = 1e-10, growing as 3.3e-14 kappa beyond kappa = 3e3 (the table method forms every
 quantity through A_0^{-1}; Section V names this instability) for at most 0.1% of the results;
-mixed: tol = max(1e-3, 10 * 2^-24 * kappa), the kappa part for at most 2% of the results.
+mixed: tol = max(3e-3, 10 * 2^-24 * kappa), the kappa part for at most 2% of the results.
 Results of well-conditioned moves with little cancellation also meet the flat bar as a plain
 relative error.
 """
@@ -20,7 +20,7 @@ from _parity import FLAT, KAPPA_ONLY_SHARE, bar_report, rel_err, replay, tol_fp6
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-MIXED_TOL = 1e-3
+MIXED_TOL = 3e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
