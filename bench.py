@@ -95,16 +95,23 @@ def sweep_work(problem, spin: int, W: int, mixed: bool, n_exc_internal: int):
 
 
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
-SWEEP_SOURCES = ("msd_kernels.cu", "msd_smalldet.cuh", "msd_records.cuh", "msd_internal.h")
+SWEEP_SOURCES = ("msd_smalldet.cuh", "msd_records.cuh")
+SWEEP_SECTION = ("// A2-A5: reference ratio, excitation sweep", "// A6: accept")
 
 
 def sweep_source_hash() -> str:
-    """SHA-256 (first 16 hex digits) of the sources the sweep kernel is compiled from."""
+    """SHA-256 (first 16 hex digits) of the code the sweep kernel is compiled from: its section of
+    msd_kernels.cu (from the A2-A5 banner to the A6 banner) and the headers it includes."""
     import hashlib
 
+    csrc = os.path.join(ROOT, "paper_1106_2456_gb300", "csrc")
     h = hashlib.sha256()
+    with open(os.path.join(csrc, "msd_kernels.cu")) as f:
+        text = f.read()
+    a, b = text.index(SWEEP_SECTION[0]), text.index(SWEEP_SECTION[1])
+    h.update(text[a:b].encode())
     for name in SWEEP_SOURCES:
-        with open(os.path.join(ROOT, "paper_1106_2456_gb300", "csrc", name), "rb") as f:
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -668,6 +675,23 @@ def run_ours(args):
             "calls": args.eloc_calls, "vs_sweep": ms_le / (ms / args.steps),
             "what": "msd_local_energy, mixed: all-electron grad/lap (one cofactor scatter per spin), "
                     "Pade-Jastrow (b_ee = b_en = 1) and Coulomb terms; vs_sweep = its time over one sweep"}
+    def per_call_ms(fn, calls):
+        fn()  # the first call allocates its workspace
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(calls):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(a0.elapsed_time(a1), dist, dev) / calls
+
+    # ---- adjoint of log|Psi| (once per parameter update of an optimisation) ----
+    gbar = torch.ones(W, dtype=torch.float64, device=dev)
+    if args.adjoint_calls > 0:
+        line["adjoint"] = {"unit": "ms per call", "calls": args.adjoint_calls,
+                           "mixed": per_call_ms(lambda: cm.backward(gbar), args.adjoint_calls),
+                           "what": "msd_backward: d log|Psi| / d c_I and d B of all walkers (refresh included)"}
     # ---- FP64 path on the same workload ----
     if not args.skip_fp64:
         cm.close()
@@ -677,6 +701,13 @@ def run_ours(args):
         line["fp64"] = {"value": job_rate(W * n_tot, ws, steps64, ms64 * 1e-3), "ms_per_step": ms64 / steps64,
                         "steps": steps64, "window": win64, "roofline": roofline("fp64", sweep64, steps64),
                         "clocks": clk64}
+        if args.eloc_calls > 0:
+            cd.set_hamiltonian(workloads.nuclear_charges(p), 1.0, 1.0)
+            eloc64 = torch.empty(W, dtype=torch.float64, device=dev)
+            line["fp64"]["local_energy_ms_per_call"] = per_call_ms(lambda: cd.local_energy_into(eloc64),
+                                                                   min(args.eloc_calls, 2))
+        if args.adjoint_calls > 0:
+            line["adjoint"]["fp64"] = per_call_ms(lambda: cd.backward(gbar), min(args.adjoint_calls, 2))
         line["mixed_speedup_vs_fp64"] = value / line["fp64"]["value"]
         # per-result difference mixed vs FP64 on a common trajectory (FP64 accept decisions) over
         # whole sweeps, so the Sherman-Morrison drift between refreshes is in the sample
@@ -739,6 +770,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1, help="sweeps through the host-buffer entry points")
     ap.add_argument("--cmp-steps", type=int, default=128, help="moves of the mixed-vs-FP64 comparison")
     ap.add_argument("--eloc-calls", type=int, default=5)
+    ap.add_argument("--adjoint-calls", type=int, default=2)
     ap.add_argument("--cpu-moves", type=int, default=30)
     ap.add_argument("--cpu-time-cap", type=float, default=25.0)
     ap.add_argument("--ref-time-cap", type=float, default=150.0)

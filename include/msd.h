@@ -278,6 +278,13 @@ msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev,
 msd_status msd_orbitals(msd_ctx* ctx, int32_t spin, int32_t nch, int32_t n_points, const double* pos_dev,
                         void* out_dev);
 
+/* Check of the failure path of the bounded device waits (the paper has no counterpart): one kernel
+ * waits on an mbarrier that nothing completes, gives up after wait_ns (1e3 .. 1e9 ns) and records
+ * the timeout in the context's status word exactly as the tensor-core kernels do, so the next
+ * msd_sync returns MSD_ERR_TIMEOUT (and clears it).  No GPU fault or hang is involved.
+ * MSD_ERR_ARG for wait_ns outside the range or a batched context. */
+msd_status msd_selftest_wait(msd_ctx* ctx, int64_t wait_ns);
+
 /*
  * VMC energy driver.  The paper runs VMC on Psi_T = exp(J) Psi_MD (Section VI) and leaves the
  * Jastrow factor J to standard methods (Section II); these calls supply a simple one and the

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 BUILDDIR = os.path.join(PKG, "_build")
-SOURCES = ["msd_kernels.cu", "msd_backward.cu", "msd_vmc.cu", "msd_orbitals_tc.cu", "msd_api.cu"]
+SOURCES = ["msd_kernels.cu", "msd_backward.cu", "msd_vmc.cu", "msd_tc.cu", "msd_api.cu"]
 # host-only translation units keep libstdc++ bounds assertions on (an out-of-range index
 # aborts with a message instead of corrupting the heap)
 HOST_CHECKED = {"msd_api.cu": ["-Xcompiler", "-D_GLIBCXX_ASSERTIONS"]}

@@ -519,7 +519,13 @@ msd_status refresh_spin(msd_ctx* c, State& st, int s) {
     const SpinConst& S = c->sp[s];
     orbitals(c, S, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->Phi);
     launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s]);
-    if (S.m > 0) launch_table(c->L(), c->mixed, c->W, S.n, S.N, st.Ainv[s], c->Phi, st.T[s]);
+    if (S.m > 0) {
+        if (c->mixed && table_tc_supported(S.n))
+            launch_table_tc(c->L(), c->W, S.n, S.N, st.Ainv[s], static_cast<const float*>(c->Phi),
+                            static_cast<float*>(st.T[s]));
+        else
+            launch_table(c->L(), c->mixed, c->W, S.n, S.N, st.Ainv[s], c->Phi, st.T[s]);
+    }
     if (c->timing) c->n_refresh++;
     st.since_refresh[s] = 0;
     st.C_valid[1 - s] = false;  // C of the other spin depends on this spin's t
@@ -1585,6 +1591,15 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
     if (S.m == 0) a.g.kmax = 0;
     launch_ratio(c->L(), c->mixed, a);
     return check_launch(c, "ratio (no allocation)");
+}
+
+msd_status msd_selftest_wait(msd_ctx* c, int64_t wait_ns) {
+    if (is_batch(c)) return fail(c, MSD_ERR_ARG, "msd_selftest_wait takes a single-system context");
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    if (wait_ns < 1000 || wait_ns > 1000000000) return fail(c, MSD_ERR_ARG, "wait_ns = %lld outside [1e3, 1e9]",
+                                                            (long long)wait_ns);
+    launch_wait_selftest(c->L(), (unsigned long long)wait_ns);
+    return check_launch(c, "wait self-test");
 }
 
 msd_status msd_orbitals(msd_ctx* c, int32_t spin, int32_t nch, int32_t n_points, const double* pos_dev,

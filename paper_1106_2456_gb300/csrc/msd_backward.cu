@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(kBB) k_dci(int W, int wchunk, long long n_det,
 // cof(T_u)[q][l] = (-1)^(q+l) det(T_u without row q and column l), each minor by the same
 // pivoted small-determinant code the sweep uses.
 template <int K, typename TT>
-__device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], double cu,
-                                                  double* Tb) {
+__device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], TT cu,
+                                                  TT* Tb) {
     if constexpr (K == 1) {
         atomicAdd(Tb + h[0] * m + p[0], cu);
     } else {
@@ -62,7 +62,7 @@ __device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int
                 int pp[K - 1];
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) pp[i] = p[i < l ? i : i + 1];
-                const double minor = double(small_det<K - 1, TT>(Ts, m, hh, pp));
+                const TT minor = small_det<K - 1, TT>(Ts, m, hh, pp);
                 atomicAdd(Tb + h[q] * m + p[l], ((q + l) & 1) ? -cu * minor : cu * minor);
             }
         }
@@ -73,8 +73,8 @@ __device__ __forceinline__ void scatter_cofactors(const TT* Ts, int m, const int
 // i.e. adj(T_u) e_q, which the pivoted elimination of the ratio sweep (adj_solve) gives for one
 // LU per column.  For K >= 5 that is far less work than K^2 separate (K-1) x (K-1) minors.
 template <int K, typename TT>
-__device__ __forceinline__ void scatter_adjugate(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], double cu,
-                                                 double* Tb) {
+__device__ __forceinline__ void scatter_adjugate(const TT* Ts, int m, const int (&h)[K], const int (&p)[K], TT cu,
+                                                 TT* Tb) {
     TT Tu[K * K];
     int id[K];
 #pragma unroll
@@ -89,22 +89,22 @@ __device__ __forceinline__ void scatter_adjugate(const TT* Ts, int m, const int 
 #pragma unroll
         for (int j = 0; j < K; ++j) e[j] = j == q ? TT(1) : TT(0);
         adj_solve<K, TT>(Tu, K, e, id, id, det, z);
-        double* row = Tb + h[q] * m;
+        TT* row = Tb + h[q] * m;
 #pragma unroll
-        for (int l = 0; l < K; ++l) atomicAdd(row + p[l], cu * double(z[l]));
+        for (int l = 0; l < K; ++l) atomicAdd(row + p[l], cu * z[l]);
     }
 }
 
 template <int K, typename TT>
 __device__ __forceinline__ void tbar_group(const ExcDev& g, const TT* Ts, int m, const TT* __restrict__ Cw,
-                                           double* Tb) {
+                                           TT* Tb) {
     const int j0 = g.goff[K], j1 = g.goff[K + 1];
     const uint8_t* rec = g.rec + g.roff[K];
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         int h[K], p[K];
         load_rec<K>(rec, j - j0, h, p);
-        const double cu = double(Cw[j]);
-        if (h[0] == kEmptyRecord || cu == 0.0) continue;
+        const TT cu = Cw[j];
+        if (h[0] == kEmptyRecord || cu == TT(0)) continue;
         if constexpr (K >= 5)
             scatter_adjugate<K, TT>(Ts, m, h, p, cu, Tb);
         else
@@ -115,26 +115,32 @@ __device__ __forceinline__ void tbar_group(const ExcDev& g, const TT* Ts, int m,
 // Orders 5-8 are rare: out of line, so that their registers do not limit orders 1-4.
 template <int K, typename TT>
 __device__ __noinline__ void tbar_group_outlined(const ExcDev& g, const TT* Ts, int m, const TT* __restrict__ Cw,
-                                                 double* Tb) {
+                                                 TT* Tb) {
     tbar_group<K, TT>(g, Ts, m, Cw, Tb);
 }
 
-constexpr int kTbarThreads = 512;  // one block per SM (the table and its adjoint fill shared memory)
-
-// Writes Tbar / S into columns n..N-1 of M[w] (n x N, row stride N).
+// Threads per block: FP64 tables and their adjoint fill an SM's shared memory (one block of 512);
+// FP32 ones take half, so two blocks of 256 share an SM.
 template <typename TT>
-__global__ void __launch_bounds__(kTbarThreads, 1) k_tbar(int n, int m, int N, ExcDev g, const TT* __restrict__ T,
-                                             const TT* __restrict__ C, const double* __restrict__ S,
-                                             double* __restrict__ M) {
+__host__ __device__ constexpr int tbar_threads() {
+    return sizeof(TT) == 4 ? 256 : 512;
+}
+
+// Writes Tbar / S into columns n..N-1 of M[w] (n x N, row stride N).  The cofactors are summed in
+// the table's precision (FP32 tables: FP32 shared-memory atomics, off the slow FP64 pipe).
+template <typename TT>
+__global__ void __launch_bounds__(tbar_threads<TT>(), sizeof(TT) == 4 ? 2 : 1)
+    k_tbar(int n, int m, int N, ExcDev g, const TT* __restrict__ T, const TT* __restrict__ C,
+           const double* __restrict__ S, double* __restrict__ M) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double* Tb = reinterpret_cast<double*>(smem);                                  // [n][m]
-    TT* Ts = reinterpret_cast<TT*>(smem + (((size_t)n * m * 8 + 15) & ~size_t(15)));  // [n][m]
+    TT* Tb = reinterpret_cast<TT*>(smem);                                                   // [n][m]
+    TT* Ts = reinterpret_cast<TT*>(smem + (((size_t)n * m * sizeof(TT) + 15) & ~size_t(15)));  // [n][m]
     const int w = blockIdx.x;
     const TT* Tw = T + (long long)w * n * m;
     const TT* Cw = C + (long long)w * g.n_exc;
     for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
         Ts[q] = Tw[q];
-        Tb[q] = g.dense1 ? double(Cw[g.goff[1] + q]) : 0.0;  // dense singles: d det T_u / d T[h][p] = 1
+        Tb[q] = g.dense1 ? Cw[g.goff[1] + q] : TT(0);  // dense singles: d det T_u / d T[h][p] = 1
     }
     __syncthreads();
     for (int k = g.dense1 ? 2 : 1; k <= g.kmax; ++k) {
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(kTbarThreads, 1) k_tbar(int n, int m, int N, E
     double* Mw = M + (long long)w * n * N;
     for (int q = threadIdx.x; q < n * m; q += blockDim.x) {
         const int c = q / m, a = q - c * m;
-        Mw[(long long)c * N + n + a] = Tb[q] * inv;
+        Mw[(long long)c * N + n + a] = double(Tb[q]) * inv;
     }
 }
 
@@ -421,7 +427,8 @@ void launch_dci(const Launch& L, bool mixed, int W, long long n_det, const int* 
 }
 
 size_t tbar_smem_bytes(bool mixed, int n, int m) {
-    return (((size_t)n * m * 8 + 15) & ~size_t(15)) + (size_t)n * m * (mixed ? 4 : 8);
+    const size_t b = mixed ? 4 : 8;
+    return (((size_t)n * m * b + 15) & ~size_t(15)) + (size_t)n * m * b;
 }
 
 void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, const ExcDev& g, const void* T,
@@ -431,14 +438,14 @@ void launch_phibar(const Launch& L, bool mixed, int W, int n, int m, int N, cons
         if (mixed) {
             cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             L.count();
-            k_tbar<float><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T),
+            k_tbar<float><<<W, tbar_threads<float>(), sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T),
                                                     static_cast<const float*>(C), S, M);
             L.count();
             k_tbar_tt<float><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const float*>(T), M);
         } else {
             cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             L.count();
-            k_tbar<double><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+            k_tbar<double><<<W, tbar_threads<double>(), sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
                                                      static_cast<const double*>(C), S, M);
             L.count();
             k_tbar_tt<double><<<W, kBB, 0, L.stream>>>(n, m, N, static_cast<const double*>(T), M);
@@ -475,12 +482,12 @@ void launch_tbar(const Launch& L, bool mixed, int W, int n, int m, int N, const 
     if (mixed) {
         cudaFuncSetAttribute(k_tbar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         L.count();
-        k_tbar<float><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T), static_cast<const float*>(C),
+        k_tbar<float><<<W, tbar_threads<float>(), sm, L.stream>>>(n, m, N, g, static_cast<const float*>(T), static_cast<const float*>(C),
                                                 S, M);
     } else {
         cudaFuncSetAttribute(k_tbar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         L.count();
-        k_tbar<double><<<W, kTbarThreads, sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
+        k_tbar<double><<<W, tbar_threads<double>(), sm, L.stream>>>(n, m, N, g, static_cast<const double*>(T),
                                                  static_cast<const double*>(C), S, M);
     }
 }

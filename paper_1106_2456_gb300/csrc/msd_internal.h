@@ -60,7 +60,7 @@ void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const
                      long long wstride, int p_off, const double4* bas, const int8_t* blm, int nb,
                      const void* B, int N, void* out);
 
-// The same orbitals on the tensor cores (FP32 path, msd_orbitals_tc.cu): B of one spin split on
+// The same orbitals on the tensor cores (FP32 path, msd_tc.cu): B of one spin split on
 // the host into three TF32 pieces in the operand layout the kernel copies (tc_split_B), TN <= 256
 // columns per tile, nT column tiles, nK chunks of 8 basis functions; out is FP32.
 struct TcPlan {
@@ -75,6 +75,14 @@ void tc_basis_pairs(int nb, const double* centers, const double* alpha, float* o
 void launch_orbitals_tc(const Launch& L, int nch, int P, int ppw, const double* pos, long long wstride, int p_off,
                         const float4* basf, const int8_t* blm, int nb, const TcPlan& t, const float* Bsplit, int N,
                         float* out);
+
+// T[w] = Ainv[w] * Phi[w][:, n:N] on the tensor cores (FP32 path; n <= 256, table_tc_supported).
+bool table_tc_supported(int n);
+void launch_table_tc(const Launch& L, int W, int n, int N, const double* Ainv, const float* Phi, float* T);
+
+// One block that waits limit_ns on an mbarrier nothing completes and sets ST_TIMEOUT (a check of the
+// bounded-wait failure path).
+void launch_wait_selftest(const Launch& L, unsigned long long limit_ns);
 
 // Gauss-Jordan inverse with partial pivoting of A_0 = Phi[w][:, :n] for every walker.
 void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv,

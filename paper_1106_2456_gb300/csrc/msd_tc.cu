@@ -1,7 +1,8 @@
-// msd_orbitals_tc.cu -- the orbital contraction of the FP32 path on the fifth-generation tensor
-// cores of sm_103a (tcgen05 MMA with the accumulator in tensor memory).
+// msd_tc.cu -- the dense contractions of the FP32 path on the fifth-generation tensor cores of
+// sm_103a (tcgen05 MMA with the accumulator in tensor memory): the orbital product and the
+// excitation table.
 //
-// Algorithm 1 step 2 evaluates the orbitals at a position: phi^a_j(r) = sum_mu chi^a_mu(r) B[mu][j]
+// Orbitals.  Algorithm 1 step 2 evaluates the orbitals at a position: phi^a_j(r) = sum_mu chi^a_mu(r) B[mu][j]
 // for the value and derivative channels a.  Over P points this is one dense product
 //   out[P NC x N] = X[P NC x nb] . B[nb x N],   row p NC + a of X = chi^a(r_p),
 // the only dense contraction on the per-move path; the refresh (NC = 1, every electron of a spin)
@@ -75,8 +76,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Wait for the mbarrier phase of the given parity to complete, at most kTcWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the mbarrier phase of the given parity to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kTcWaitNs) {
     const unsigned long long t0 = global_ns();
     for (;;) {
         uint32_t done;
@@ -86,7 +87,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kTcWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -366,6 +367,148 @@ __global__ void __launch_bounds__(kTcThreads) k_orbitals_tc_batched(const BatchS
                          static_cast<float*>(o.out), B.status, tl.y, tl.z);
 }
 
+// A wait that runs out on purpose: an mbarrier that expects one arrival nobody makes, waited on
+// with the bounded wait of the tensor-core kernels; on expiry the same status bit is set.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = __syncthreads_and(threadIdx.x == 0 ? mbar_wait(b, 0u, limit_ns) : true) != 0;
+    if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+// ------------------------------------------------------------------------------------------
+// Excitation table T = A_0^{-1} Phi_virt (Algorithm 1 step 3: one matrix product per walker)
+// ------------------------------------------------------------------------------------------
+// Computed transposed, D[a][c] = T[c][a] = sum_r Phi[r][n + a] Ainv[c][r]: M = virtual orbitals
+// (128 per tile), N = occupied orbitals (n rounded up to 16, <= 256), K = electrons r in chunks
+// of 32.  Both operands are staged by the threads in three TF32 pieces of their FP32 values
+// (A_0^{-1} rounded to FP32, as the FP32 table is stored); the six piece products of size
+// >= 2^-22 accumulate in tensor memory, so the product has FP32 accuracy.  The epilogue writes
+// rows c of T with consecutive lanes on consecutive a (coalesced).
+constexpr int kTbK = 32;                      // electrons per chunk
+constexpr int kTbABytes = kTcM * kTbK * 4;    // one piece of the Phi_virt^T chunk: 16 KB
+
+__host__ __device__ constexpr uint32_t kmajor32_offset(int row, int k) {
+    return (uint32_t)((row >> 3) * (kTbK * 32) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void split3(float x, float& p0, float& p1, float& p2) {
+    p0 = tf32_rna(x);
+    const float r = x - p0;
+    p1 = tf32_rna(r);
+    p2 = tf32_rna(r - p1);
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_table_tc(int n, int N, int NP, const double* __restrict__ Ainv,
+                                                        const float* __restrict__ Phi, float* __restrict__ T,
+                                                        int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int m = N - n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w = blockIdx.y, a0 = blockIdx.x * kTcM;
+    const uint32_t b_bytes = (uint32_t)NP * kTbK * 4;
+    const uint32_t ncols = NP <= 32 ? 32u : NP <= 64 ? 64u : NP <= 128 ? 128u : 256u;
+    const uint32_t sbase = smem_u32(smem), bar = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const double* Aw = Ainv + (long long)w * n * n;
+    const float* Pw = Phi + (long long)w * n * N;
+    const uint32_t id = tf32_idesc(NP, kTcM);
+    const int nK = (n + kTbK - 1) / kTbK;
+    uint32_t phase = 0u;
+    bool ok = true;
+    for (int kc = 0; kc < nK && ok; ++kc) {
+        const int r0 = kc * kTbK;
+        // A: rows a (virtual orbitals of the tile), K = electrons r: Phi[r][n + a].  A warp covers 8
+        // rows x 4 electrons, so each store fills the 32 banks of one core matrix.
+        for (int i = tid; i < kTcM * kTbK; i += kTcThreads) {
+            const int g = i >> 5, l = i & 31;
+            const int row = 8 * (g % (kTcM / 8)) + (l & 7), k = 4 * (g / (kTcM / 8)) + (l >> 3);
+            const int a = a0 + row, r = r0 + k;
+            const float x = (a < m && r < n) ? Pw[(long long)r * N + n + a] : 0.0f;
+            float p0, p1, p2;
+            split3(x, p0, p1, p2);
+            const uint32_t off = kmajor32_offset(row, k);
+            *reinterpret_cast<float*>(smem + off) = p0;
+            *reinterpret_cast<float*>(smem + kTbABytes + off) = p1;
+            *reinterpret_cast<float*>(smem + 2 * kTbABytes + off) = p2;
+        }
+        // B: rows c (occupied orbitals), K = electrons r: A_0^{-1}[c][r] rounded to FP32 (the table is
+        // stored in FP32) and split there; same warp layout as A
+        unsigned char* sbp = smem + 3 * kTbABytes;
+        for (int i = tid; i < NP * kTbK; i += kTcThreads) {
+            const int g = i >> 5, l = i & 31;
+            const int c = 8 * (g % (NP / 8)) + (l & 7), k = 4 * (g / (NP / 8)) + (l >> 3), r = r0 + k;
+            const float v = (c < n && r < n) ? float(Aw[(long long)c * n + r]) : 0.0f;
+            float p0, p1, p2;
+            split3(v, p0, p1, p2);
+            const uint32_t off = kmajor32_offset(c, k);
+            *reinterpret_cast<float*>(sbp + off) = p0;
+            *reinterpret_cast<float*>(sbp + b_bytes + off) = p1;
+            *reinterpret_cast<float*>(sbp + 2 * b_bytes + off) = p2;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int pa[6] = {0, 0, 1, 1, 0, 2};
+            const int pb[6] = {0, 1, 0, 1, 2, 0};
+#pragma unroll
+            for (int st = 0; st < kTbK / kTcK; ++st)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const uint64_t ad = smem_desc(sbase + pa[q] * kTbABytes + st * 256, 128, kTbK * 32);
+                    const uint64_t bd = smem_desc(sbase + 3 * kTbABytes + pb[q] * b_bytes + st * 256, 128, kTbK * 32);
+                    mma_tf32(tmem, ad, bd, id, (kc > 0 || st > 0 || q > 0) ? 1u : 0u);
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        // the next chunk overwrites the operands: wait for these MMAs (one thread, then the block)
+        ok = __syncthreads_and(tid == 0 ? mbar_wait(bar, phase) : true) != 0;
+        phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // lanes are virtual orbitals a; warp w takes column blocks of parity w / 4
+        const int a = a0 + 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        float* Tw = T + (long long)w * n * m;
+        for (int cb = 32 * (warp >> 2); cb < NP; cb += 64) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)cb, v);
+            if (a < m)
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (cb + j < n) Tw[(long long)(cb + j) * m + a] = __uint_as_float(v[j]);
+        }
+    } else if (tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 float host_tf32(float x) {
     uint32_t u;
     std::memcpy(&u, &x, 4);
@@ -454,6 +597,24 @@ void launch_orbitals_tc_batched(const Launch& L, const BatchPlan& P, int t, int 
         cudaFuncSetAttribute(k_orbitals_tc_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.tc_smem);
         k_orbitals_tc_batched<1><<<P.n_tc_tiles, kTcThreads, P.tc_smem, L.stream>>>(P.sys, P.tc_tiles, t, rnew);
     }
+}
+
+void launch_wait_selftest(const Launch& L, unsigned long long limit_ns) {
+    L.count();
+    k_wait_selftest<<<1, 32, 0, L.stream>>>(limit_ns, L.status);
+}
+
+bool table_tc_supported(int n) { return n >= 1 && n <= 256; }
+
+void launch_table_tc(const Launch& L, int W, int n, int N, const double* Ainv, const float* Phi, float* T) {
+    const int m = N - n;
+    if (m <= 0 || W <= 0) return;
+    const int NP = (n + 15) / 16 * 16;
+    const size_t sm = (size_t)3 * kTbABytes + (size_t)3 * NP * kTbK * 4;
+    const dim3 grid((unsigned)((m + kTcM - 1) / kTcM), (unsigned)W);
+    L.count();
+    cudaFuncSetAttribute(k_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_table_tc<<<grid, kTcThreads, sm, L.stream>>>(n, N, NP, Ainv, Phi, T, L.status);
 }
 
 }  // namespace msd

@@ -109,6 +109,7 @@ def load_library():
         "msd_timing_stop": ([vp, vp, vp, vp], i32),
         "msd_timing_counts": ([vp, vp], i32),
         "msd_orbitals": ([vp, i32, i32, i32, vp, vp], i32),
+        "msd_selftest_wait": ([vp, ctypes.c_int64], i32),
         "msd_set_hamiltonian": ([vp, vp, vp], i32),
         "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
         "msd_local_energy": ([vp, vp, vp], i32),
@@ -394,6 +395,10 @@ class MSD:
         self._check(self.lib.msd_orbitals(self.ctx, int(spin), int(nch), P, _dptr(pos, torch.float64, (P, 3), "pos"),
                                           out.data_ptr()))
         return out
+
+    def selftest_wait(self, wait_ns: int):
+        """msd_selftest_wait: a device wait that runs out; the next sync raises MSD_ERR_TIMEOUT."""
+        self._check(self.lib.msd_selftest_wait(self.ctx, int(wait_ns)))
 
     def timing_counts(self):
         """(from-scratch refreshes of a spin, CI contractions) since timing_start."""

@@ -57,6 +57,7 @@ def tol_mixed(kappa):
 FLAT = {"fp64": 1e-10, "mixed": 3e-3}
 # Largest share of a test's results that may pass only through the kappa allowance of the bar.
 KAPPA_ONLY_SHARE = {"fp64": 1e-3, "mixed": 2e-2}
+KAPPA_EDGES = (0.0, 1e2, 1e3, 1e4, 1e5, 1e6, 1e7, 1e8, float("inf"))
 
 
 def bar_report(out, precision: str, label: str = "") -> Dict:
@@ -80,7 +81,11 @@ def bar_report(out, precision: str, label: str = "") -> Dict:
                     "max_plain": float(ep.max(initial=0.0)),
                     "n_plain_well": int(plain_sel.sum()),
                     "max_plain_well": float(ep[plain_sel].max(initial=0.0)),
-                    "max_kappa": float(kp.max(initial=0.0))}
+                    "max_kappa": float(kp.max(initial=0.0)),
+                    "by_kappa": [{"kappa_le": hi, "n": int(((kp > lo) & (kp <= hi)).sum()),
+                                  "max_scaled": float(es[(kp > lo) & (kp <= hi)].max(initial=0.0))}
+                                 for lo, hi in zip(KAPPA_EDGES[:-1], KAPPA_EDGES[1:])
+                                 if ((kp > lo) & (kp <= hi)).any()]}
     path = os.environ.get("MSD_PARITY_REPORT")
     if path:
         with open(path, "a") as f:

@@ -267,6 +267,26 @@ def test_propose_and_metropolis_helpers():
     ctx.close()
 
 
+def test_bounded_wait_reports_timeout():
+    """A device wait that runs out (an mbarrier nothing completes, 1 ms limit) sets the status the
+    tensor-core kernels set on a timeout: msd_sync raises MSD_ERR_TIMEOUT once, and the context
+    keeps working."""
+    w = wl.make_workload("water", n_walkers=8)
+    ctx = msd.MSD(w.problem, w.n_walkers, "mixed")
+    ctx.set_positions(torch.tensor(w.R0, device="cuda"))
+    ctx.sync()
+    ctx.selftest_wait(1_000_000)
+    with pytest.raises(msd.MSDError, match="MSD_ERR_TIMEOUT"):
+        ctx.sync()
+    ctx.sync()  # cleared
+    with pytest.raises(msd.MSDError, match="MSD_ERR_ARG"):
+        ctx.selftest_wait(10)
+    r, g, l = ctx.ratio(0, torch.tensor(w.R0[:, 0] + 0.1, device="cuda"))
+    assert bool(torch.isfinite(r).all())
+    ctx.sync()
+    ctx.close()
+
+
 def test_error_paths_without_faults():
     w = wl.make_workload("water", n_walkers=8)
     p = w.problem
