@@ -336,9 +336,11 @@ def run_batched(args):
                 lap=torch.empty(W, dtype=torch.float64, device=dev),
                 acc=torch.empty(W, dtype=torch.uint8, device=dev))
 
-    def run(prec, steps):
+    def run(prec, steps, rescue_slots=0):
         b = msd.MSDBatch([w.problem for w in systems], [w.n_walkers for w in systems], prec,
                          refresh_K=[w.refresh_K for w in systems], stream=stream)
+        if rescue_slots:
+            b.set_rescue(rescue_slots)
         b.set_positions(R0)
 
         def step(t):
@@ -367,13 +369,14 @@ def run_batched(args):
         if clk:
             clk.stop()
         ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        # a walker whose reference matrix becomes nearly singular (Section V) can drive the FP32
-        # path to a non-finite ratio; the library flags it and the run goes on: report it
+        # a walker whose reference matrix becomes nearly singular (Section V) is held in FP64 on the
+        # FP32 path; anything still non-finite is flagged by the library and reported here
         try:
             b.sync()
             flagged = None
         except msd.MSDError as ex:
             flagged = str(ex)
+        rescue = b.rescue_stats() if rescue_slots else None
         b.close()
         # algorithmic work of every system's sweeps in these steps
         F = B = 0.0
@@ -385,9 +388,9 @@ def run_batched(args):
                 f, by = sweep_work(p, sp, w.n_walkers, prec == "mixed", int(plan[sp][0]))
                 F += f
                 B += by
-        return ms, sweep_ms, n_sweep, n_launch, F, B, (clk.summary(w0, w1) if clk else None), flagged
+        return ms, sweep_ms, n_sweep, n_launch, F, B, (clk.summary(w0, w1) if clk else None), flagged, rescue
 
-    ms, sweep_ms, n_sweep, n_launch, F, B, clocks, flagged = run("mixed", args.steps)
+    ms, sweep_ms, n_sweep, n_launch, F, B, clocks, flagged, rescue = run("mixed", args.steps)
     sec = ms * 1e-3
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     hbm = {"achieved": B / sec / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": B / sec / 1e9 / hbm_peak,
@@ -407,9 +410,16 @@ def run_batched(args):
                        "precision": "mixed", "parallelism": f"replicas x{ws}, systems on 8 streams",
                        "l2": "inputs exceed L2"},
             "roofline": roof, "gpu_launches": int(n_launch), "clocks": clocks, "status": flagged or "ok"}
+    if args.rescue_slots > 0:
+        steps_r = min(args.steps, args.rescue_steps)
+        ms_r, _, _, _, _, _, clk_r, flagged_r, rescue = run("mixed", steps_r, args.rescue_slots)
+        line["rescue_on"] = {"value": job_rate(W, ws, steps_r, ms_r * 1e-3), "ms_per_step": ms_r / steps_r,
+                             "steps": steps_r, "status": flagged_r or "ok", "stats": rescue,
+                             "what": "ill-conditioned walkers held in FP64 (msd_set_rescue, up to "
+                                     f"{args.rescue_slots} per system)"}
     if not args.skip_fp64:
         steps64 = min(args.steps, args.fp64_steps)
-        ms64, _, _, _, _, _, clk64, flagged64 = run("fp64", steps64)
+        ms64, _, _, _, _, _, clk64, flagged64, _ = run("fp64", steps64)
         line["fp64"] = {"value": job_rate(W, ws, steps64, ms64 * 1e-3), "ms_per_step": ms64 / steps64,
                         "steps": steps64, "clocks": clk64, "status": flagged64 or "ok"}
     if rank == 0:
@@ -634,6 +644,16 @@ def run_ours(args):
             "window": window,
             "roofline": roofline("mixed", sweep_ms, args.steps),
             "gpu_launches": int(n_launch), "clocks": clocks}
+    # ---- the same with ill-conditioned walkers held in FP64 (msd_set_rescue) ----
+    if args.rescue_slots > 0:
+        cr = msd.MSD(p, W, "mixed", refresh_K=K, stream=stream)
+        cr.set_rescue(args.rescue_slots)
+        cr.set_positions(torch.tensor(R0, device=dev))
+        ms_r, _, _, _, clk_r, win_r = timed(cr, min(args.steps, args.rescue_steps))
+        line["rescue_on"] = {"value": job_rate(W * n_tot, ws, min(args.steps, args.rescue_steps), ms_r * 1e-3),
+                             "ms_per_step": ms_r / min(args.steps, args.rescue_steps), "slots": args.rescue_slots,
+                             "stats": cr.rescue_stats(), "window": win_r, "clocks": clk_r}
+        cr.close()
     # ---- end to end through the host-buffer C ABI ----
     if args.e2e_steps > 0:
         e2e_steps = min(args.steps, args.e2e_steps)
@@ -711,38 +731,50 @@ def run_ours(args):
         line["mixed_speedup_vs_fp64"] = value / line["fp64"]["value"]
         # per-result difference mixed vs FP64 on a common trajectory (FP64 accept decisions) over
         # whole sweeps, so the Sherman-Morrison drift between refreshes is in the sample
-        cd.set_positions(torch.tensor(R0, device=dev))
-        cm = make("mixed")
-        errs = {"ratio": [], "grad": [], "lap": []}
-        big, same = [], []
-        for t in range(args.cmp_steps):
-            e = t % n_tot
-            cd.propose(e, eta[t], wl.tau, bufs["rnew"])
-            r64, g64, l64 = cd.ratio(e, bufs["rnew"])
-            r32, g32, l32 = cm.ratio(e, bufs["rnew"])
-            for key, a, b in (("ratio", r32, r64), ("grad", g32, g64), ("lap", l32, l64)):
-                # per walker: |a - b| / |b|, the gradient by its Euclidean norm
-                d = (a - b).reshape(W, -1).norm(dim=1)
-                errs[key].append((d / b.reshape(W, -1).norm(dim=1).clamp_min(1e-300)).cpu().numpy())
-            big.append((r64.abs() >= 0.1).cpu().numpy())
-            same.append(((u[t] < r32 * r32) == (u[t] < r64 * r64)).cpu().numpy())
-            cd.metropolis(u[t], r64, bufs["acc"])
-            cd.accept(e, bufs["acc"])
-            cm.accept(e, bufs["acc"])
-        big = np.concatenate(big)
-        cmp = {}
-        for k, v in errs.items():
-            v = np.concatenate(v)
-            cmp[k] = {"median_rel": float(np.median(v)), "p90_rel": float(np.percentile(v, 90)),
-                      "p99_rel": float(np.percentile(v, 99)),
-                      "p99_rel_ratio_ge_0.1": float(np.percentile(v[big], 99))}
-        cmp["moves"] = args.cmp_steps
-        cmp["ratio_ge_0.1_share"] = float(big.mean())
-        cmp["metropolis_decisions_equal"] = float(np.concatenate(same).mean())
+        def compare(rescue_slots):
+            cd.set_positions(torch.tensor(R0, device=dev))
+            cmx = msd.MSD(p, W, "mixed", refresh_K=K, stream=stream)
+            if rescue_slots:
+                cmx.set_rescue(rescue_slots)
+            cmx.set_positions(torch.tensor(R0, device=dev))
+            errs = {"ratio": [], "grad": [], "lap": []}
+            big, same = [], []
+            for t in range(args.cmp_steps):
+                e = t % n_tot
+                cd.propose(e, eta[t], wl.tau, bufs["rnew"])
+                r64, g64, l64 = cd.ratio(e, bufs["rnew"])
+                r32, g32, l32 = cmx.ratio(e, bufs["rnew"])
+                for key, a, b in (("ratio", r32, r64), ("grad", g32, g64), ("lap", l32, l64)):
+                    # per walker: |a - b| / |b|, the gradient by its Euclidean norm
+                    d = (a - b).reshape(W, -1).norm(dim=1)
+                    errs[key].append((d / b.reshape(W, -1).norm(dim=1).clamp_min(1e-300)).cpu().numpy())
+                big.append((r64.abs() >= 0.1).cpu().numpy())
+                same.append(((u[t] < r32 * r32) == (u[t] < r64 * r64)).cpu().numpy())
+                cd.metropolis(u[t], r64, bufs["acc"])
+                cd.accept(e, bufs["acc"])
+                cmx.accept(e, bufs["acc"])
+            big = np.concatenate(big)
+            cmp = {}
+            for k, v in errs.items():
+                v = np.concatenate(v)
+                cmp[k] = {"median_rel": float(np.median(v)), "p90_rel": float(np.percentile(v, 90)),
+                          "p99_rel": float(np.percentile(v, 99)), "p999_rel": float(np.percentile(v, 99.9)),
+                          "p99_rel_ratio_ge_0.1": float(np.percentile(v[big], 99))}
+            cmp["moves"] = args.cmp_steps
+            cmp["ratio_ge_0.1_share"] = float(big.mean())
+            cmp["metropolis_decisions_equal"] = float(np.concatenate(same).mean())
+            if rescue_slots:
+                cmp["rescue"] = cmx.rescue_stats()
+            cmx.close()
+            return cmp
+
+        cmp = compare(0)
         cmp["note"] = ("relative difference per walker-move (grad: Euclidean norm); the tail comes from moves "
                        "whose ratio is a small difference of large CI terms; p99_rel_ratio_ge_0.1 keeps the moves "
                        "with |ratio| >= 0.1; metropolis_decisions_equal: same accept decision from the same uniform")
         line["mixed_vs_fp64"] = cmp
+        if args.rescue_slots > 0:
+            line["mixed_vs_fp64_rescue"] = compare(args.rescue_slots)
         cd.close()
     cm.close()
     # ---- FP64 CPU oracle on a bounded sample ----
@@ -771,6 +803,9 @@ def main():
     ap.add_argument("--cmp-steps", type=int, default=128, help="moves of the mixed-vs-FP64 comparison")
     ap.add_argument("--eloc-calls", type=int, default=5)
     ap.add_argument("--adjoint-calls", type=int, default=2)
+    ap.add_argument("--rescue-slots", type=int, default=32,
+                    help="FP64 slots of the extra legs with ill-conditioned walkers held in FP64 (0: skip them)")
+    ap.add_argument("--rescue-steps", type=int, default=4, help="timed sweeps of the rescue leg")
     ap.add_argument("--cpu-moves", type=int, default=30)
     ap.add_argument("--cpu-time-cap", type=float, default=25.0)
     ap.add_argument("--ref-time-cap", type=float, default=150.0)

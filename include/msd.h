@@ -278,6 +278,26 @@ msd_status msd_ratio_noalloc(msd_ctx* ctx, int32_t elec, const double* rnew_dev,
 msd_status msd_orbitals(msd_ctx* ctx, int32_t spin, int32_t nch, int32_t n_points, const double* pos_dev,
                         void* out_dev);
 
+/* Walkers the FP32 path cannot represent (Section V: a reference matrix A_0 close to singular; the
+ * FP32 orbitals and table then carry an error of order 2^-24 cond(A_0) or more).  At every refresh
+ * of a spin the FP32 path estimates cond(A_0) = ||A_0||_inf ||A_0^{-1}||_inf per walker and spin
+ * (from its FP64 inverse).  A walker whose larger estimate exceeds kappa_hold is held in an FP64
+ * context of `slots` walkers: its msd_ratio, msd_accept, msd_get_state and msd_grad_lap results
+ * come from there, until a later refresh finds both estimates below kappa_release.  The held set
+ * changes only at refreshes (which then synchronise the stream); the FP64 context is built at
+ * the first hold (an allocation).  msd_eval_batch, msd_backward and msd_ratio_noalloc use the FP32
+ * state of every walker.  The FP64 work runs on an internal stream forked from and joined back into
+ * the context's, overlapping the FP32 kernels of the same call.  Off by default (slots = 0); at
+ * most min(W, 32) slots; suggested thresholds kappa_hold = 1e7, kappa_release = 1e5.  Releases
+ * every held walker (they are held again at once if still beyond kappa_hold).  MSD_ERR_ARG for
+ * other precisions, slots beyond min(W, 32) or 1 < kappa_release <= kappa_hold violated.  A
+ * batched context applies it to every system. */
+msd_status msd_set_rescue(msd_ctx* ctx, int32_t slots, double kappa_hold, double kappa_release);
+
+/* out[0] = walkers held now, [1] = holds so far, [2] = releases so far, [3] = walkers beyond
+ * kappa_hold that found no free slot (counted per refresh), [4] = slots; summed over systems. */
+msd_status msd_rescue_stats(const msd_ctx* ctx, int64_t* out);
+
 /* Check of the failure path of the bounded device waits (the paper has no counterpart): one kernel
  * waits on an mbarrier that nothing completes, gives up after wait_ns (1e3 .. 1e9 ns) and records
  * the timeout in the context's status word exactly as the tensor-core kernels do, so the next

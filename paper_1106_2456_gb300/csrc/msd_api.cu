@@ -58,11 +58,79 @@ struct State {
     bool C_valid[2] = {false, false};
 };
 
+// Deep copy of a problem's host arrays (for building the FP64 rescue context later).
+struct ProblemCopy {
+    msd_problem p{};
+    std::vector<double> nuc, alpha, B0, B1, ci;
+    std::vector<int32_t> center, off0, off1, up, dn;
+    std::vector<int8_t> lm;
+    std::vector<uint8_t> h0, h1, p0, p1;
+    void take(const msd_problem* q) {
+        p = *q;
+        nuc.assign(q->nuc_xyz, q->nuc_xyz + 3 * (size_t)q->n_nuc);
+        center.assign(q->bas_center, q->bas_center + q->n_basis);
+        lm.assign(q->bas_lm, q->bas_lm + q->n_basis);
+        alpha.assign(q->bas_alpha, q->bas_alpha + q->n_basis);
+        B0.assign(q->B[0], q->B[0] + (size_t)q->n_basis * q->n_orb[0]);
+        B1.assign(q->B[1], q->B[1] + (size_t)q->n_basis * q->n_orb[1]);
+        off0.assign(q->exc_off[0], q->exc_off[0] + q->n_exc[0] + 1);
+        off1.assign(q->exc_off[1], q->exc_off[1] + q->n_exc[1] + 1);
+        h0.assign(q->exc_holes[0], q->exc_holes[0] + off0.back());
+        p0.assign(q->exc_parts[0], q->exc_parts[0] + off0.back());
+        h1.assign(q->exc_holes[1], q->exc_holes[1] + off1.back());
+        p1.assign(q->exc_parts[1], q->exc_parts[1] + off1.back());
+        up.assign(q->det_up, q->det_up + q->n_det);
+        dn.assign(q->det_dn, q->det_dn + q->n_det);
+        ci.assign(q->ci, q->ci + q->n_det);
+        p.nuc_xyz = nuc.data();
+        p.bas_center = center.data();
+        p.bas_lm = lm.data();
+        p.bas_alpha = alpha.data();
+        p.B[0] = B0.data();
+        p.B[1] = B1.data();
+        p.exc_off[0] = off0.data();
+        p.exc_off[1] = off1.data();
+        p.exc_holes[0] = h0.data();
+        p.exc_holes[1] = h1.data();
+        p.exc_parts[0] = p0.data();
+        p.exc_parts[1] = p1.data();
+        p.det_up = up.data();
+        p.det_dn = dn.data();
+        p.ci = ci.data();
+    }
+};
+
+// FP32 path: walkers whose reference matrix the FP32 table cannot represent are held, from one
+// refresh to a later one, in an FP64 context of a few slots (Section V: a nearly singular A_0).
+struct Rescue {
+    bool enabled = false;
+    int slots = 0;
+    double k_demote = 1e7, k_promote = 1e5;  // ||A_0||_inf ||A_0^{-1}||_inf thresholds
+    msd_ctx* fb = nullptr;                   // the FP64 context (built at the first demotion)
+    std::vector<int> walker_of;              // slot -> walker, -1 free
+    std::vector<int> slot_of;                // walker -> slot, -1
+    int active = 0;                          // slots in use (they come first in d_walker_of)
+    int* d_slot_of = nullptr;                // [W]
+    int* d_walker_of = nullptr;              // [slots]; free slots repeat an active walker
+    int* d_status_scratch = nullptr;         // status of the FP32 kernels while some walkers are held
+    double* cond[2] = {nullptr, nullptr};    // [W] per spin, from the last refresh
+    double *rnew = nullptr, *ratio = nullptr, *grad = nullptr, *lap = nullptr, *R = nullptr;
+    double *logabs = nullptr, *sign = nullptr, *ga_grad = nullptr, *ga_lap = nullptr;
+    uint8_t* acc = nullptr;
+    cudaStream_t side = nullptr;             // the FP64 context's stream, forked from the caller's
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    long long demotions = 0, promotions = 0, overflow = 0;
+    int alloc_slots = 0;  // slots the scratch arrays hold
+    ProblemCopy prob;
+    int slots_max() const { return alloc_slots; }
+};
+
 }  // namespace
 
 struct msd_ctx {
     int W = 0, n_tot = 0, nb = 0, K = 1;
     int device = -1;  // the CUDA device current at msd_init (whose memory holds the context)
+    Rescue rs;        // FP32 path: walkers held in FP64
     bool mixed = false;
     size_t tb = 8;  // bytes of the table/orbital type
     cudaStream_t stream = nullptr;
@@ -118,6 +186,7 @@ struct msd_ctx {
     std::vector<cudaEvent_t> bevents;                       // [0] fork, [1 + i] join of stream i
     BatchPlan bplan;                                        // single-launch descriptors of the systems
     double* b_rnew = nullptr;                               // [W][3] positions of the current proposal
+    int* b_status_scratch = nullptr;                        // status word of the FP32 batched ratio launch
     std::vector<void*> allocs;
     std::string err;
     // measurement: kernel launch count and events around the excitation-sweep kernel
@@ -518,7 +587,8 @@ msd_status upload_split_B(msd_ctx* c, SpinConst& S, const double* B_host) {
 msd_status refresh_spin(msd_ctx* c, State& st, int s) {
     const SpinConst& S = c->sp[s];
     orbitals(c, S, 1, c->W * S.n, S.n, st.R, (long long)c->n_tot * 3, S.off, c->Phi);
-    launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s]);
+    launch_inverse(c->L(), c->mixed, c->W, S.n, S.N, c->Phi, st.Ainv[s], st.logdet[s], st.sgn[s],
+                   (c->rs.enabled && &st == &c->st) ? c->rs.cond[s] : nullptr);
     if (S.m > 0) {
         if (c->mixed && table_tc_supported(S.n))
             launch_table_tc(c->L(), c->W, S.n, S.N, st.Ainv[s], static_cast<const float*>(c->Phi),
@@ -616,6 +686,213 @@ msd_status canon_C(msd_ctx* c, State& st, int s, bool with_S) {
 
 int spin_of(const msd_ctx* c, int e) { return e < c->sp[0].n ? 0 : 1; }
 
+// ------------------------------------------------------------------------------------------
+// FP64 rescue of ill-conditioned walkers on the FP32 path
+// ------------------------------------------------------------------------------------------
+bool rescue_on(const msd_ctx* c) { return c->rs.enabled && c->rs.active > 0; }
+
+// Per-walker arrays of a mixed single-system context; slots = min(W, 32).
+msd_status rescue_alloc(msd_ctx* c, const msd_problem* p) {
+    Rescue& r = c->rs;
+    r.enabled = c->mixed;
+    if (!r.enabled) return MSD_OK;
+    r.slots = 0;  // off until msd_set_rescue
+    r.alloc_slots = std::min(c->W, 32);
+    r.walker_of.assign(r.alloc_slots, -1);
+    r.slot_of.assign(c->W, -1);
+    const size_t W = c->W, S = r.alloc_slots, nt = c->n_tot;
+    TRY(dalloc(c, &r.cond[0], W));
+    TRY(dalloc(c, &r.cond[1], W));
+    TRY(dalloc(c, &r.d_slot_of, W));
+    TRY(dalloc(c, &r.d_walker_of, S));
+    TRY(dalloc(c, &r.d_status_scratch, 1));
+    TRY(dalloc(c, &r.rnew, S * 3));
+    TRY(dalloc(c, &r.ratio, S));
+    TRY(dalloc(c, &r.grad, S * 3));
+    TRY(dalloc(c, &r.lap, S));
+    TRY(dalloc(c, &r.R, S * nt * 3));
+    TRY(dalloc(c, &r.logabs, S));
+    TRY(dalloc(c, &r.sign, S));
+    TRY(dalloc(c, &r.acc, S));
+    TRY(dalloc(c, &r.ga_grad, S * nt * 3));
+    TRY(dalloc(c, &r.ga_lap, S * nt));
+    if (cudaMemset(r.cond[0], 0, sizeof(double) * W) != cudaSuccess ||
+        cudaMemset(r.cond[1], 0, sizeof(double) * W) != cudaSuccess ||
+        cudaMemset(r.d_slot_of, 0xFF, sizeof(int) * W) != cudaSuccess)
+        return fail(c, MSD_ERR_CUDA, "rescue memset");
+    r.prob.take(p);
+    return MSD_OK;
+}
+
+msd_status rescue_upload_maps(msd_ctx* c) {
+    Rescue& r = c->rs;
+    std::vector<int> wo(r.slots);
+    for (int q = 0; q < r.slots; ++q) wo[q] = q < r.active ? r.walker_of[q] : (r.active ? r.walker_of[0] : 0);
+    cudaError_t e = cudaMemcpyAsync(r.d_walker_of, wo.data(), sizeof(int) * r.slots, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.d_slot_of, r.slot_of.data(), sizeof(int) * c->W, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors may change before the copy ran
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "rescue maps: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+// Release every held walker (new positions).
+msd_status rescue_reset(msd_ctx* c) {
+    Rescue& r = c->rs;
+    if (!r.enabled) return MSD_OK;
+    std::fill(r.walker_of.begin(), r.walker_of.end(), -1);
+    std::fill(r.slot_of.begin(), r.slot_of.end(), -1);
+    r.active = 0;
+    return rescue_upload_maps(c);
+}
+
+// The FP64 context runs on its own stream, forked from and joined back into the caller's, so its
+// work overlaps the FP32 kernels of the same call.
+msd_status side_fork(msd_ctx* c) {
+    Rescue& r = c->rs;
+    cudaError_t e = cudaEventRecord(r.ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(r.side, r.ev_fork, 0);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "rescue fork: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+msd_status side_join(msd_ctx* c) {
+    Rescue& r = c->rs;
+    cudaError_t e = cudaEventRecord(r.ev_join, r.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, r.ev_join, 0);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "rescue join: %s", cudaGetErrorString(e));
+    return MSD_OK;
+}
+
+Launch side_launch(msd_ctx* c) {
+    Launch l = c->L();
+    l.stream = c->rs.side;
+    return l;
+}
+
+// After a refresh of the main state: hold walkers whose condition estimate (the larger of the two
+// spins' latest) exceeds k_demote, release held ones below k_promote, and rebuild the FP64
+// context at the held walkers' current positions when the set changed.  Synchronises the stream.
+msd_status rescue_update(msd_ctx* c) {
+    Rescue& r = c->rs;
+    if (!r.enabled || r.slots == 0) return MSD_OK;
+    const size_t W = c->W;
+    std::vector<double> k0(W), k1(W);
+    cudaError_t e = cudaMemcpyAsync(k0.data(), r.cond[0], sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(k1.data(), r.cond[1], sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "rescue read: %s", cudaGetErrorString(e));
+    bool changed = false;
+    for (size_t w = 0; w < W; ++w) {
+        const double k = std::max(k0[w], k1[w]);
+        const int q = r.slot_of[w];
+        if (q < 0 && !(k <= r.k_demote)) {  // also a non-finite estimate
+            int free = -1;
+            for (int j = 0; j < r.slots && free < 0; ++j)
+                if (r.walker_of[j] < 0) free = j;
+            if (free < 0) {
+                ++r.overflow;
+                continue;
+            }
+            r.walker_of[free] = (int)w;
+            r.slot_of[w] = free;
+            ++r.demotions;
+            changed = true;
+        } else if (q >= 0 && k < r.k_promote) {
+            r.walker_of[q] = -1;
+            r.slot_of[w] = -1;
+            ++r.promotions;
+            changed = true;
+        }
+    }
+    if (!changed) return MSD_OK;
+    // held walkers first, in slot order
+    std::vector<int> held;
+    for (int j = 0; j < r.slots; ++j)
+        if (r.walker_of[j] >= 0) held.push_back(r.walker_of[j]);
+    r.active = (int)held.size();
+    std::fill(r.walker_of.begin(), r.walker_of.end(), -1);
+    std::fill(r.slot_of.begin(), r.slot_of.end(), -1);
+    for (int j = 0; j < r.active; ++j) {
+        r.walker_of[j] = held[j];
+        r.slot_of[held[j]] = j;
+    }
+    TRY(rescue_upload_maps(c));
+    if (r.active == 0) return MSD_OK;
+    if (!r.side) {
+        if (cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(c, MSD_ERR_CUDA, "rescue stream");
+    }
+    if (!r.fb) {
+        msd_problem q = r.prob.p;
+        q.prec = MSD_FP64;
+        q.n_walkers = r.slots;
+        q.refresh_K = c->K;
+        q.cuda_stream = r.side;
+        const msd_status st = msd_init(&q, 1, &r.fb);
+        if (st != MSD_OK) return fail(c, st, "FP64 rescue context: %s", msd_last_error(nullptr));
+    }
+    TRY(side_fork(c));
+    launch_gather_rows(side_launch(c), r.slots, r.d_walker_of, c->n_tot * 3, c->st.R, r.R);
+    const msd_status st = msd_set_positions(r.fb, r.R);
+    if (st != MSD_OK) return fail(c, st, "FP64 rescue: %s", r.fb->err.c_str());
+    TRY(side_join(c));
+    return check_launch(c, "rescue rebuild");
+}
+
+msd_status rescue_fail(msd_ctx* c, msd_status st) {
+    return fail(c, st, "FP64 rescue: %s", c->rs.fb ? c->rs.fb->err.c_str() : "");
+}
+
+// The held walkers' ratio (and gradient, laplacian) from the FP64 context: started on its stream
+// before the FP32 sweep, written over the FP32 values after it, then the finiteness check the
+// FP32 launch was relieved of.
+msd_status rescue_ratio_begin(msd_ctx* c, int elec, const double* rnew_dev, bool with_grad) {
+    Rescue& r = c->rs;
+    TRY(side_fork(c));
+    launch_gather_rows(side_launch(c), r.slots, r.d_walker_of, 3, rnew_dev, r.rnew);
+    const msd_status st = msd_ratio(r.fb, elec, r.rnew, r.ratio, with_grad ? r.grad : nullptr,
+                                    with_grad ? r.lap : nullptr);
+    if (st != MSD_OK) return rescue_fail(c, st);
+    return MSD_OK;
+}
+
+msd_status rescue_ratio_end(msd_ctx* c, double* ratio, double* grad, double* lap) {
+    Rescue& r = c->rs;
+    TRY(side_join(c));
+    launch_scatter_rows(c->L(), r.active, r.d_walker_of, 1, r.ratio, ratio);
+    if (grad) {
+        launch_scatter_rows(c->L(), r.active, r.d_walker_of, 3, r.grad, grad);
+        launch_scatter_rows(c->L(), r.active, r.d_walker_of, 1, r.lap, lap);
+    }
+    launch_check_finite(c->L(), c->W, ratio);
+    return check_launch(c, "rescue ratio");
+}
+
+msd_status rescue_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* ratio, double* grad, double* lap) {
+    TRY(rescue_ratio_begin(c, elec, rnew_dev, grad != nullptr));
+    return rescue_ratio_end(c, ratio, grad, lap);
+}
+
+// The held walkers' accept on the FP64 stream, overlapping the FP32 accept.
+msd_status rescue_accept_begin(msd_ctx* c, int elec, const uint8_t* accept_dev) {
+    Rescue& r = c->rs;
+    TRY(side_fork(c));
+    launch_gather_bytes(side_launch(c), r.slots, r.d_walker_of, accept_dev, r.acc);
+    const msd_status st = msd_accept(r.fb, elec, r.acc);
+    if (st != MSD_OK) return rescue_fail(c, st);
+    return MSD_OK;
+}
+
+msd_status rescue_accept(msd_ctx* c, int elec, const uint8_t* accept_dev) {
+    TRY(rescue_accept_begin(c, elec, accept_dev));
+    TRY(side_join(c));
+    return check_launch(c, "rescue accept");
+}
+
 // Orbitals at the current position of electron e, then the bordered sweep with rnew = r_e.
 msd_status grad_lap_one(msd_ctx* c, State& st, int e, double* grad, long long gs, double* lap, long long ls) {
     const int s = spin_of(c, e);
@@ -699,6 +976,9 @@ msd_status build_batch_plan(msd_ctx* c) {
         B.W = sc->W;
         B.w_off = (int)c->w_off[q];
         B.status = sc->d_status;
+        // FP32 path: the ratio launch reports into a scratch word; the outputs are checked after the
+        // held walkers' FP64 values replaced theirs
+        B.ratio_status = c->mixed ? c->b_status_scratch : nullptr;
         B.R = sc->st.R;
         int Nmax = 0, nT = 0;
         for (int s = 0; s < 2; ++s) {
@@ -719,6 +999,7 @@ msd_status build_batch_plan(msd_ctx* c) {
             b.phi = sc->phi_new; b.rho = sc->rho; b.num = sc->num; b.y0 = sc->y0;
             b.Ainv = sc->st.Ainv[s]; b.T = sc->st.T[s]; b.R = sc->st.R; b.logdet = sc->st.logdet[s];
             b.sgn = sc->st.sgn[s]; b.S = sc->st.S;
+            b.skip = sc->rs.d_slot_of;
             sys_smem[q] = std::max(sys_smem[q], ratio_smem_bytes(c->mixed, S.n, S.m, NCH));
             rsm = std::max(rsm, sys_smem[q]);
             asm_ = std::max(asm_, accept_smem_bytes(S.n));
@@ -809,6 +1090,7 @@ msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* rat
                 r = refresh_spin(sc, st, s);
                 if (r == MSD_OK) r = ensure_C(sc, st, s);
                 if (r == MSD_OK) r = recompute_S(sc, st, s);
+                if (r == MSD_OK) r = rescue_update(sc);
             } else {
                 r = ensure_C(sc, st, s);
             }
@@ -831,6 +1113,27 @@ msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* rat
     else
         launch_orbitals_batched(c->L(), c->mixed, c->bplan, elec, nch, c->b_rnew);
     launch_ratio_batched(c->L_sweep(), c->mixed, c->bplan, elec, nch, ratio_dev, grad_dev, lap_dev);
+    TRY(check_launch(c, "batched ratio"));
+    if (c->mixed) {
+        bool any = false;
+        for (msd_ctx* sc : c->sub) any = any || rescue_on(sc);
+        if (any) {
+            TRY(batch_fork(c));
+            for (size_t q = 0; q < c->sub.size(); ++q) {
+                msd_ctx* sc = c->sub[q];
+                if (!rescue_on(sc)) continue;
+                const long long w = c->w_off[q];
+                const msd_status r = rescue_ratio(sc, elec % sc->n_tot, rnew_dev + 3 * w, ratio_dev + w,
+                                                  grad_dev ? grad_dev + 3 * w : nullptr, lap_dev ? lap_dev + w : nullptr);
+                if (r != MSD_OK) {
+                    batch_join(c);
+                    return fail(c, r, "system %zu: %s", q, sc->err.c_str());
+                }
+            }
+            TRY(batch_join(c));
+        }
+        launch_check_finite_batched(c->L(), c->bplan, c->W, ratio_dev);
+    }
     return check_launch(c, "batched ratio");
 }
 
@@ -849,7 +1152,23 @@ msd_status batch_accept(msd_ctx* c, int elec, const uint8_t* accept_dev) {
         sc->prop_valid = false;
     }
     launch_accept_batched(c->L(), c->mixed, c->bplan, elec, nch, accept_dev, c->b_rnew);
-    return check_launch(c, "batched accept");
+    TRY(check_launch(c, "batched accept"));
+    bool any = false;
+    for (msd_ctx* sc : c->sub) any = any || rescue_on(sc);
+    if (any) {
+        TRY(batch_fork(c));
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            msd_ctx* sc = c->sub[q];
+            if (!rescue_on(sc)) continue;
+            const msd_status r = rescue_accept(sc, elec % sc->n_tot, accept_dev + c->w_off[q]);
+            if (r != MSD_OK) {
+                batch_join(c);
+                return fail(c, r, "system %zu: %s", q, sc->err.c_str());
+            }
+        }
+        TRY(batch_join(c));
+    }
+    return MSD_OK;
 }
 
 msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
@@ -893,6 +1212,7 @@ msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
         b += (long long)q.n_basis * (q.n_orb[0] + q.n_orb[1]);
     }
     c->W = (int)w;
+    if (dalloc(c, &c->b_status_scratch, 1) != MSD_OK) return bail(MSD_ERR_OOM);
     if (build_batch_plan(c) != MSD_OK) return bail(MSD_ERR_CUDA);
     *out = c;
     return MSD_OK;
@@ -985,6 +1305,7 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     if ((st = dalloc(c, &c->d_status, 1)) != MSD_OK) return bail(st);
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(c, MSD_ERR_CUDA, "memset"));
     if ((st = alloc_state(c, c->st)) != MSD_OK) return bail(st);
+    if ((st = rescue_alloc(c, p)) != MSD_OK) return bail(st);
     if (c->canon) {
         for (int s = 0; s < 2; ++s) {
             const SpinConst& S = c->sp[s];
@@ -1050,7 +1371,9 @@ msd_status msd_set_positions(msd_ctx* c, const double* R_dev) {
         return batch_each(c, [&](int s, msd_ctx* sc) { return msd_set_positions(sc, R_dev + c->r_off[s]); });
     if (!c || !R_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     c->prop_valid = false;
-    return set_positions(c, c->st, R_dev);
+    TRY(rescue_reset(c));
+    TRY(set_positions(c, c->st, R_dev));
+    return rescue_update(c);
 }
 
 msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
@@ -1094,6 +1417,7 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
         TRY(refresh_spin(c, st, s));
         TRY(ensure_C(c, st, s));
         TRY(recompute_S(c, st, s));
+        TRY(rescue_update(c));
     } else {
         TRY(ensure_C(c, st, s));
     }
@@ -1108,8 +1432,17 @@ msd_status msd_ratio(msd_ctx* c, int32_t elec, const double* rnew_dev, double* r
     a.ratio = ratio_dev; a.rs = 1; a.grad = grad_dev; a.gs = 3; a.lap = lap_dev; a.ls = 1;
     a.rho = c->rho; a.num = c->num; a.y0 = c->y0;
     if (S.m == 0) a.g.kmax = 0;
-    launch_ratio(c->L_sweep(), c->mixed, a);
+    {
+        // while walkers are held in FP64, their FP32 values are overwritten and checked afterwards
+        Launch lr = c->L_sweep();
+        if (rescue_on(c)) {
+            lr.status = c->rs.d_status_scratch;
+            TRY(rescue_ratio_begin(c, elec, rnew_dev, grad_dev != nullptr));
+        }
+        launch_ratio(lr, c->mixed, a);
+    }
     TRY(check_launch(c, "ratio"));
+    if (rescue_on(c)) TRY(rescue_ratio_end(c, ratio_dev, grad_dev, lap_dev));
     c->prop_elec = elec;
     c->prop_nch = nch;
     c->prop_valid = true;
@@ -1140,13 +1473,40 @@ msd_status msd_accept(msd_ctx* c, int32_t elec, const uint8_t* accept_dev) {
     a.accept = accept_dev; a.phi = c->phi_new; a.nch = c->prop_nch; a.rho = c->rho; a.num = c->num; a.y0 = c->y0;
     a.rnew = c->rnew; a.Ainv = st.Ainv[s]; a.T = st.T[s]; a.R = st.R; a.logdet = st.logdet[s]; a.sgn = st.sgn[s];
     a.S = st.S;
+    if (rescue_on(c)) {
+        a.skip = c->rs.d_slot_of;
+        TRY(rescue_accept_begin(c, elec, accept_dev));
+    }
     launch_accept(c->L(), c->mixed, a);
     st.C_valid[1 - s] = false;
     c->prop_valid = false;
+    if (rescue_on(c)) TRY(side_join(c));
     return check_launch(c, "accept");
 }
 
+static msd_status grad_lap_main(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev);
+
 msd_status msd_grad_lap(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev) {
+    TRY(grad_lap_main(c, elec, grad_dev, lap_dev));
+    if (c && !is_batch(c) && rescue_on(c)) {
+        // held walkers: from the FP64 context
+        Rescue& r = c->rs;
+        TRY(side_fork(c));
+        const bool all = elec < 0;
+        double* g = all ? r.ga_grad : r.grad;
+        double* l = all ? r.ga_lap : r.lap;
+        const msd_status st = msd_grad_lap(r.fb, elec, g, l);
+        if (st != MSD_OK) return rescue_fail(c, st);
+        TRY(side_join(c));
+        const int k = all ? c->n_tot : 1;
+        launch_scatter_rows(c->L(), r.active, r.d_walker_of, 3 * k, g, grad_dev);
+        launch_scatter_rows(c->L(), r.active, r.d_walker_of, k, l, lap_dev);
+        return check_launch(c, "rescue grad/lap");
+    }
+    return MSD_OK;
+}
+
+static msd_status grad_lap_main(msd_ctx* c, int32_t elec, double* grad_dev, double* lap_dev) {
     if (c && c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
     if (is_batch(c) && grad_dev && lap_dev && elec >= -1)
         return batch_each(c, [&](int s, msd_ctx* sc) {
@@ -1228,6 +1588,15 @@ msd_status msd_get_state(msd_ctx* c, double* R_dev, double* logabs_dev, double* 
     }
     if (logabs_dev || sign_dev)
         launch_state(c->L(), c->W, st.logdet[0], st.sgn[0], st.logdet[1], st.sgn[1], st.S, logabs_dev, sign_dev);
+    if (rescue_on(c) && (logabs_dev || sign_dev)) {
+        Rescue& r = c->rs;
+        TRY(side_fork(c));
+        const msd_status rs_st = msd_get_state(r.fb, nullptr, r.logabs, r.sign);
+        if (rs_st != MSD_OK) return rescue_fail(c, rs_st);
+        TRY(side_join(c));
+        if (logabs_dev) launch_scatter_rows(c->L(), r.active, r.d_walker_of, 1, r.logabs, logabs_dev);
+        if (sign_dev) launch_scatter_rows(c->L(), r.active, r.d_walker_of, 1, r.sign, sign_dev);
+    }
     return check_launch(c, "get_state");
 }
 
@@ -1320,6 +1689,10 @@ msd_status msd_sync(msd_ctx* c) {
         return MSD_OK;
     }
     if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    if (c->rs.fb) {
+        const msd_status fs = msd_sync(c->rs.fb);
+        if (fs != MSD_OK) return rescue_fail(c, fs);
+    }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     int status = 0;
@@ -1545,6 +1918,16 @@ void msd_destroy(msd_ctx* c) {
         c->bevents.clear();
     }
     if (!c) return;
+    if (c->rs.fb) {
+        msd_destroy(c->rs.fb);
+        c->rs.fb = nullptr;
+    }
+    if (c->rs.side) {
+        cudaStreamSynchronize(c->rs.side);
+        cudaStreamDestroy(c->rs.side);
+        cudaEventDestroy(c->rs.ev_fork);
+        cudaEventDestroy(c->rs.ev_join);
+    }
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
@@ -1591,6 +1974,50 @@ msd_status msd_ratio_noalloc(msd_ctx* c, int32_t elec, const double* rnew_dev, d
     if (S.m == 0) a.g.kmax = 0;
     launch_ratio(c->L(), c->mixed, a);
     return check_launch(c, "ratio (no allocation)");
+}
+
+msd_status msd_set_rescue(msd_ctx* c, int32_t slots, double kappa_hold, double kappa_release) {
+    if (is_batch(c)) {
+        for (size_t q = 0; q < c->sub.size(); ++q) {
+            const msd_status st = msd_set_rescue(c->sub[q], slots, kappa_hold, kappa_release);
+            if (st != MSD_OK) return fail(c, st, "system %zu: %s", q, c->sub[q]->err.c_str());
+        }
+        return MSD_OK;
+    }
+    if (!c) return fail(c, MSD_ERR_ARG, "NULL context");
+    if (!c->mixed) return fail(c, MSD_ERR_ARG, "only the mixed-precision path holds walkers in FP64");
+    if (slots < 0 || slots > c->rs.slots_max())
+        return fail(c, MSD_ERR_ARG, "slots = %d outside [0, %d]", slots, c->rs.slots_max());
+    if (!(kappa_hold > 1.0) || !(kappa_release > 1.0) || !(kappa_release <= kappa_hold))
+        return fail(c, MSD_ERR_ARG, "need 1 < kappa_release <= kappa_hold");
+    Rescue& r = c->rs;
+    TRY(rescue_reset(c));
+    if (r.fb && slots != r.slots) {  // its walker count is the slot count
+        msd_destroy(r.fb);
+        r.fb = nullptr;
+    }
+    r.slots = slots;
+    r.k_demote = kappa_hold;
+    r.k_promote = kappa_release;
+    if (c->st.ready) return rescue_update(c);  // from the condition estimates of the last refreshes
+    return MSD_OK;
+}
+
+msd_status msd_rescue_stats(const msd_ctx* c, int64_t* out) {
+    if (!c || !out) return MSD_ERR_ARG;
+    for (int i = 0; i < 5; ++i) out[i] = 0;
+    auto add = [&](const msd_ctx* x) {
+        out[0] += x->rs.active;
+        out[1] += x->rs.demotions;
+        out[2] += x->rs.promotions;
+        out[3] += x->rs.overflow;
+        out[4] += x->rs.slots;
+    };
+    if (!c->sub.empty())
+        for (const msd_ctx* sc : c->sub) add(sc);
+    else
+        add(c);
+    return MSD_OK;
 }
 
 msd_status msd_selftest_wait(msd_ctx* c, int64_t wait_ns) {
@@ -1703,10 +2130,23 @@ msd_status msd_set_params(msd_ctx* c, const double* ci_host, const double* B_up_
         }
     }
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "parameter upload: %s", cudaGetErrorString(e));
+    if (c->rs.enabled) {
+        // the FP64 context, and the copy it is built from, take the same parameters
+        if (ci_host) std::copy(ci_host, ci_host + c->n_det, c->rs.prob.ci.begin());
+        if (B_up_host) {
+            std::copy(B_up_host, B_up_host + c->rs.prob.B0.size(), c->rs.prob.B0.begin());
+            std::copy(B_dn_host, B_dn_host + c->rs.prob.B1.size(), c->rs.prob.B1.begin());
+        }
+        if (c->rs.fb) {
+            const msd_status fs = msd_set_params(c->rs.fb, ci_host, B_up_host, B_dn_host);
+            if (fs != MSD_OK) return rescue_fail(c, fs);
+        }
+    }
     c->prop_valid = false;
     c->scratch.C_valid[0] = c->scratch.C_valid[1] = false;
     if (!c->st.ready) return MSD_OK;
-    return rebuild(c, c->st);
+    TRY(rebuild(c, c->st));
+    return rescue_update(c);
 }
 
 }  // extern "C"

@@ -84,9 +84,10 @@ void launch_table_tc(const Launch& L, int W, int n, int N, const double* Ainv, c
 // bounded-wait failure path).
 void launch_wait_selftest(const Launch& L, unsigned long long limit_ns);
 
-// Gauss-Jordan inverse with partial pivoting of A_0 = Phi[w][:, :n] for every walker.
+// Gauss-Jordan inverse with partial pivoting of A_0 = Phi[w][:, :n] for every walker; cond (nullable)
+// receives ||A_0||_inf ||A_0^{-1}||_inf per walker.
 void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv,
-                    double* logdet, double* sgn);
+                    double* logdet, double* sgn, double* cond = nullptr);
 
 // T[w] = Ainv[w] * Phi[w][:, n:N].
 void launch_table(const Launch& L, bool mixed, int W, int n, int N, const double* Ainv, const void* Phi,
@@ -139,11 +140,22 @@ struct AcceptArgs {
     double* logdet;
     double* sgn;
     double* S;
+    const int* skip = nullptr;  // [W] walkers held elsewhere (>= 0): their flags are not raised (nullable)
 };
 void launch_accept(const Launch& L, bool mixed, const AcceptArgs& a);
 
 void launch_propose(const Launch& L, int W, int n_tot, int elec, const double* R, const double* eta, double tau,
                     double* rnew);
+// Rows of walkers in and out of the FP64 rescue context: dst[s][:] = src[map[s]][:] (gather, every
+// slot) and dst[map[s]][:] = src[s][:] for s < n_real (scatter).
+void launch_gather_rows(const Launch& L, int n_slots, const int* map, int row, const double* src, double* dst);
+void launch_gather_bytes(const Launch& L, int n_slots, const int* map, const uint8_t* src, uint8_t* dst);
+void launch_scatter_rows(const Launch& L, int n_real, const int* map, int row, const double* src, double* dst);
+// ST_NONFINITE if any of ratio[0..W) is not finite.
+void launch_check_finite(const Launch& L, int W, const double* ratio);
+struct BatchPlan;
+// The same for a batch: a non-finite ratio of walker w flags its system's status.
+void launch_check_finite_batched(const Launch& L, const BatchPlan& P, int W, const double* ratio);
 void launch_metropolis(const Launch& L, int W, const double* u, const double* ratio, uint8_t* accept);
 void launch_state(const Launch& L, int W, const double* ld0, const double* sg0, const double* ld1,
                   const double* sg1, const double* S, double* logabs, double* sign);
@@ -167,6 +179,7 @@ struct OrbArgs {
 struct BatchSys {
     int n_tot, n_up, W, w_off;  // electrons, walkers, offset of the walkers in concatenated arrays
     int* status;                // the system's status word
+    int* ratio_status;          // where the ratio launch reports instead (nullable: status)
     const double* R;            // [W][n_tot][3]
     OrbArgs orb[2];             // per spin
     RatioArgs ratio[2];         // per spin, without row, nch and outputs

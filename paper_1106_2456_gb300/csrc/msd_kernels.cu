@@ -168,10 +168,27 @@ __global__ void __launch_bounds__(256) k_orbitals(int P, int ppw, const double* 
 // ------------------------------------------------------------------------------------------
 // A7: from-scratch inverse of A_0 (Gauss-Jordan with partial pivoting, FP64, one block per walker)
 // ------------------------------------------------------------------------------------------
+// Block-wide maximum of one value per thread (every thread receives it); red holds 32 doubles.
+__device__ __forceinline__ double block_max(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    v = 0.0;
+    for (int q = 0; q < nw; ++q) v = fmax(v, red[q]);
+    return v;
+}
+
+// cond_out (nullable): ||A_0||_inf ||A_0^{-1}||_inf, the infinity-norm condition number (infinite
+// when a pivot vanished) -- the estimate by which the FP32 path decides which walkers it can
+// represent.
 template <typename TO>
 __device__ __forceinline__ void inverse_block(int n, int N, const TO* __restrict__ src, const int* cols,
                                               double* __restrict__ dst, double* __restrict__ logdet_out,
-                                              double* __restrict__ sgn_out, int* __restrict__ status) {
+                                              double* __restrict__ sgn_out, int* __restrict__ status,
+                                              double* __restrict__ cond_out = nullptr) {
     // A[r][c] = src[r * N + col(c)], col(c) = cols ? cols[c] : c (a shared-memory map)
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = n + 1;
@@ -192,6 +209,19 @@ __device__ __forceinline__ void inverse_block(int n, int N, const TO* __restrict
             a[c * ld + r] = v;  // a = A_0^T
             amax = fmax(amax, fabs(v));
         }
+    __shared__ double s_normA;
+    if (cond_out) {
+        __syncthreads();
+        double rs = 0.0;  // largest row sum of |A_0|: row r is column r of a
+        for (int r = tid; r < n; r += bd) {
+            double t = 0.0;
+            for (int c = 0; c < n; ++c) t += fabs(a[c * ld + r]);
+            rs = fmax(rs, t);
+        }
+        rs = block_max(rs, s_amax);
+        if (tid == 0) s_normA = rs;
+        __syncthreads();
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (tx == 0) s_amax[ty] = amax;
@@ -268,6 +298,16 @@ __device__ __forceinline__ void inverse_block(int n, int N, const TO* __restrict
     // a now holds (A_0^T)^{-1} = (A_0^{-1})^T; store A_0^{-1}[c][r] = a[r][c]
     for (int c = ty; c < n; c += ny)
         for (int r = tx; r < n; r += 32) dst[c * n + r] = a[r * ld + c];
+    if (cond_out) {
+        double rs = 0.0;  // largest row sum of |A_0^{-1}|: row c is column c of a
+        for (int c = tid; c < n; c += bd) {
+            double t = 0.0;
+            for (int r = 0; r < n; ++r) t += fabs(a[r * ld + c]);
+            rs = fmax(rs, t);
+        }
+        rs = block_max(rs, s_amax);
+        if (tid == 0) *cond_out = s_bad ? INFINITY : s_normA * rs;
+    }
     if (tid == 0) {
         *logdet_out = s_bad ? -INFINITY : s_logdet;
         *sgn_out = s_bad ? 0.0 : s_sign;
@@ -278,10 +318,11 @@ __device__ __forceinline__ void inverse_block(int n, int N, const TO* __restrict
 template <typename TO>
 __global__ void __launch_bounds__(kBlock) k_inverse(int n, int N, const TO* __restrict__ Phi,
                                                     double* __restrict__ Ainv, double* __restrict__ logdet,
-                                                    double* __restrict__ sgn, int* __restrict__ status) {
+                                                    double* __restrict__ sgn, int* __restrict__ status,
+                                                    double* __restrict__ cond) {
     const int w = blockIdx.x;
     inverse_block<TO>(n, N, Phi + (long long)w * n * N, nullptr, Ainv + (long long)w * n * n, logdet + w, sgn + w,
-                      status);
+                      status, cond ? cond + w : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -995,7 +1036,7 @@ __device__ __forceinline__ void accept_block(const AcceptArgs& a, const int w, i
         }
     }
     if (tid == 0) {
-        if (!(rho != 0.0) || !isfinite(rho)) atomicOr(status, ST_SINGULAR);
+        if ((!(rho != 0.0) || !isfinite(rho)) && !(a.skip && a.skip[w] >= 0)) atomicOr(status, ST_SINGULAR);
         a.logdet[w] += log(fabs(rho));
         if (rho < 0.0) a.sgn[w] = -a.sgn[w];
         a.S[w] = a.num[(long long)w * NCH] * irho;
@@ -1014,6 +1055,39 @@ __global__ void k_propose(int W, int n_tot, int elec, const double* __restrict__
     if (i >= W * 3) return;
     const int w = i / 3, d = i - w * 3;
     rnew[i] = fma(tau, eta[i], R[((long long)w * n_tot + elec) * 3 + d]);
+}
+
+__global__ void k_gather_rows(int n, const int* __restrict__ map, int row, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * row) return;
+    const int s = int(i / row), k = int(i - (long long)s * row);
+    dst[i] = src[(long long)map[s] * row + k];
+}
+
+__global__ void k_gather_bytes(int n, const int* __restrict__ map, const uint8_t* __restrict__ src,
+                               uint8_t* __restrict__ dst) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) dst[s] = src[map[s]];
+}
+
+__global__ void k_scatter_rows(int n, const int* __restrict__ map, int row, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * row) return;
+    const int s = int(i / row), k = int(i - (long long)s * row);
+    dst[(long long)map[s] * row + k] = src[i];
+}
+
+__global__ void k_check_finite_batched(int W, const double* __restrict__ ratio, const int* __restrict__ wsys,
+                                       const BatchSys* __restrict__ sys) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W && !isfinite(ratio[w])) atomicOr(sys[wsys[w]].status, ST_NONFINITE);
+}
+
+__global__ void k_check_finite(int W, const double* __restrict__ ratio, int* __restrict__ status) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W && !isfinite(ratio[w])) atomicOr(status, ST_NONFINITE);
 }
 
 __global__ void k_metropolis(int W, const double* __restrict__ u, const double* __restrict__ ratio,
@@ -1074,7 +1148,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS
         sa.gs = 3;
         sa.lap = lap ? lap + B.w_off : nullptr;
         sa.ls = 1;
-        s_status = B.status;
+        s_status = B.ratio_status ? B.ratio_status : B.status;
     }
     __syncthreads();
     ratio_block<TO, TT, NC>(sa, bw.y, s_status);
@@ -1146,18 +1220,18 @@ void launch_orbitals(const Launch& L, bool mixed, int nch, int P, int ppw, const
 }
 
 void launch_inverse(const Launch& L, bool mixed, int W, int n, int N, const void* Phi, double* Ainv, double* logdet,
-                    double* sgn) {
+                    double* sgn, double* cond) {
     const size_t sm = (size_t)n * (n + 1) * 8 + (size_t)n * 8 + (size_t)n * 4 + 16;
     if (mixed) {
         set_smem(k_inverse<float>, sm);
         L.count();
         k_inverse<float><<<W, kBlock, sm, L.stream>>>(n, N, static_cast<const float*>(Phi), Ainv, logdet, sgn,
-                                                      L.status);
+                                                      L.status, cond);
     } else {
         set_smem(k_inverse<double>, sm);
         L.count();
         k_inverse<double><<<W, kBlock, sm, L.stream>>>(n, N, static_cast<const double*>(Phi), Ainv, logdet, sgn,
-                                                       L.status);
+                                                       L.status, cond);
     }
 }
 
@@ -1276,6 +1350,36 @@ void launch_propose(const Launch& L, int W, int n_tot, int elec, const double* R
                     double* rnew) {
     L.count();
     k_propose<<<(W * 3 + 255) / 256, 256, 0, L.stream>>>(W, n_tot, elec, R, eta, tau, rnew);
+}
+
+void launch_gather_rows(const Launch& L, int n_slots, const int* map, int row, const double* src, double* dst) {
+    const long long tot = (long long)n_slots * row;
+    if (tot <= 0) return;
+    L.count();
+    k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, L.stream>>>(n_slots, map, row, src, dst);
+}
+
+void launch_gather_bytes(const Launch& L, int n_slots, const int* map, const uint8_t* src, uint8_t* dst) {
+    if (n_slots <= 0) return;
+    L.count();
+    k_gather_bytes<<<(n_slots + 255) / 256, 256, 0, L.stream>>>(n_slots, map, src, dst);
+}
+
+void launch_scatter_rows(const Launch& L, int n_real, const int* map, int row, const double* src, double* dst) {
+    const long long tot = (long long)n_real * row;
+    if (tot <= 0) return;
+    L.count();
+    k_scatter_rows<<<(unsigned)((tot + 255) / 256), 256, 0, L.stream>>>(n_real, map, row, src, dst);
+}
+
+void launch_check_finite_batched(const Launch& L, const BatchPlan& P, int W, const double* ratio) {
+    L.count();
+    k_check_finite_batched<<<(W + 255) / 256, 256, 0, L.stream>>>(W, ratio, P.wsys, P.sys);
+}
+
+void launch_check_finite(const Launch& L, int W, const double* ratio) {
+    L.count();
+    k_check_finite<<<(W + 255) / 256, 256, 0, L.stream>>>(W, ratio, L.status);
 }
 
 void launch_metropolis(const Launch& L, int W, const double* u, const double* ratio, uint8_t* accept) {

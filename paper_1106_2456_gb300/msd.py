@@ -110,6 +110,8 @@ def load_library():
         "msd_timing_counts": ([vp, vp], i32),
         "msd_orbitals": ([vp, i32, i32, i32, vp, vp], i32),
         "msd_selftest_wait": ([vp, ctypes.c_int64], i32),
+        "msd_set_rescue": ([vp, i32, ctypes.c_double, ctypes.c_double], i32),
+        "msd_rescue_stats": ([vp, vp], i32),
         "msd_set_hamiltonian": ([vp, vp, vp], i32),
         "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
         "msd_local_energy": ([vp, vp, vp], i32),
@@ -396,6 +398,16 @@ class MSD:
                                           out.data_ptr()))
         return out
 
+    def set_rescue(self, slots: int, kappa_hold: float = 1e7, kappa_release: float = 1e5):
+        """msd_set_rescue: walkers beyond kappa_hold are held in an FP64 context of `slots` walkers."""
+        self._check(self.lib.msd_set_rescue(self.ctx, int(slots), float(kappa_hold), float(kappa_release)))
+
+    def rescue_stats(self) -> dict:
+        out = np.zeros(5, dtype=np.int64)
+        self._check(self.lib.msd_rescue_stats(self.ctx, out.ctypes.data))
+        return dict(held=int(out[0]), holds=int(out[1]), releases=int(out[2]), overflow=int(out[3]),
+                    slots=int(out[4]))
+
     def selftest_wait(self, wait_ns: int):
         """msd_selftest_wait: a device wait that runs out; the next sync raises MSD_ERR_TIMEOUT."""
         self._check(self.lib.msd_selftest_wait(self.ctx, int(wait_ns)))
@@ -524,3 +536,12 @@ class MSDBatch:
         out = np.zeros(2, dtype=np.int64)
         self._check(self.lib.msd_timing_counts(self.ctx, out.ctypes.data))
         return int(out[0]), int(out[1])
+
+    def set_rescue(self, slots: int, kappa_hold: float = 1e7, kappa_release: float = 1e5):
+        self._check(self.lib.msd_set_rescue(self.ctx, int(slots), float(kappa_hold), float(kappa_release)))
+
+    def rescue_stats(self) -> dict:
+        out = np.zeros(5, dtype=np.int64)
+        self._check(self.lib.msd_rescue_stats(self.ctx, out.ctypes.data))
+        return dict(held=int(out[0]), holds=int(out[1]), releases=int(out[2]), overflow=int(out[3]),
+                    slots=int(out[4]))

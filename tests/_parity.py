@@ -94,19 +94,24 @@ def bar_report(out, precision: str, label: str = "") -> Dict:
 
 
 def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = None, refresh_K: Optional[int] = None,
-           elec_order: Optional[Sequence[int]] = None, step_offset: int = 0) -> Dict[str, List[float]]:
+           elec_order: Optional[Sequence[int]] = None, step_offset: int = 0, setup=None,
+           bar: Optional[str] = None) -> Dict[str, List[float]]:
     """Run n_steps single-electron moves on the GPU for all walkers; compare the walkers in
     `check` (default: all) with the oracle after every step.  Returns, per result kind and
     per step, the worst relative error and the worst ratio of error to the tolerance of the
-    precision at that walker's conditioning (<= 1 passes)."""
-    tol_fn = tol_mixed if precision == "mixed" else tol_fp64
+    precision at that walker's conditioning (<= 1 passes).  setup(ctx) runs before the positions
+    are set; bar ("fp64" or "mixed") overrides the precision whose bar is applied."""
+    tol_fn = tol_mixed if (bar or precision) == "mixed" else tol_fp64
     p = wl.problem
     W = wl.n_walkers
     idx = np.arange(W) if check is None else np.asarray(check)
     K = wl.refresh_K if refresh_K is None else refresh_K
     ctx = msd.MSD(p, W, precision, refresh_K=K)
+    if setup is not None:
+        setup(ctx)
     R = torch.tensor(wl.R0, device="cuda")
     ctx.set_positions(R)
+    out_ctx_stats = ctx.rescue_stats() if precision == "mixed" else None
     orc = oracle.Oracle(p)
     Rh = wl.R0.copy()
     cur = orc.eval(Rh[idx])
@@ -120,6 +125,7 @@ def replay(wl, precision: str, n_steps: int, check: Optional[Sequence[int]] = No
     out["logabs0"] = float(np.max(np.abs(la.cpu().numpy()[idx] - cur["logabs"]) /
                                   (tol_fn(kap0) * np.maximum(1.0, cur["absum"][:, 0]))))
     out["sign0_ok"] = bool(np.all(sg.cpu().numpy()[idx] == cur["sign"]))
+    out["rescue0"] = out_ctx_stats
     eta, u = wl.proposals(n_steps + step_offset)
     eta, u = eta[step_offset:], u[step_offset:]
     order = list(range(p.n_tot)) if elec_order is None else list(elec_order)

@@ -313,3 +313,44 @@ def test_error_paths_without_faults():
         ctx.sync()
     ctx.sync()  # status cleared
     ctx.close()
+
+
+def _near_singular_water(W=16, held=(3, 7), gap=1e-6):
+    """Water walkers in which two up electrons of the listed walkers almost coincide: their up
+    reference matrix has two nearly equal rows (Section V's nearly singular A_0)."""
+    w = wl.make_workload("water", n_walkers=W)
+    R0 = w.R0.copy()
+    for k in held:
+        R0[k, 1] = R0[k, 0] + gap * np.array([1.0, -2.0, 1.5])
+    return wl.dataclasses.replace(w, R0=R0)
+
+
+def test_mixed_holds_ill_conditioned_walkers_in_fp64():
+    """FP32 path with walkers whose cond(A_0) is far beyond what FP32 can carry: they are held in
+    the FP64 context, and their ratios, gradients and laplacians over moves of the other spin
+    (which leave the up matrices as they are) meet the FP64 bar (with its kappa allowance: these
+    walkers are the ill-conditioned case) against the oracle; the other walkers meet the mixed bar.
+    On the FP32 path alone the same walkers are off by orders of magnitude more."""
+    held = (3, 7)
+    w = _near_singular_water(held=held)
+    setup = lambda c: c.set_rescue(8, 1e5, 1e4)
+    order = [5, 6, 7, 8, 9, 5, 6, 7]  # down electrons only, within one down refresh period
+    out = replay(w, "mixed", n_steps=len(order), check=list(held), elec_order=order, setup=setup, bar="fp64")
+    rep = bar_report(out, "fp64", "held walkers")
+    print("held:", out["rescue0"], "largest kappa", max(out["kappa"]),
+          {k: rep[k]["max_scaled"] for k in ("ratio", "grad", "lap")})
+    assert out["rescue0"]["held"] == len(held)
+    for key in ("ratio", "grad", "lap"):
+        assert rep[key]["fail"] == 0, (key, rep[key])
+    assert out["sign0_ok"] and out["sign_final_ok"] and out["R_final_err"] == 0.0
+    assert out["logabs0"] <= 1.0 and out["logabs_final"] <= 1.0
+    rest = [k for k in range(w.n_walkers) if k not in held]
+    out = replay(w, "mixed", n_steps=len(order), check=rest, elec_order=order, setup=setup)
+    _assert(out, MIXED_TOL, "other walkers mixed")
+    # the same walkers on the FP32 path alone
+    off = replay(w, "mixed", n_steps=len(order), check=list(held), elec_order=order,
+                 setup=lambda c: c.set_rescue(0, 1e5, 1e4))
+    held_err = max(rep[k]["max_scaled"] for k in ("ratio", "grad", "lap"))
+    alone = max(max(off[k]) for k in ("ratio", "grad", "lap"))
+    print(f"held walkers: largest error {held_err:.2e} in FP64, {alone:.2e} on the FP32 path alone")
+    assert alone > 1e-6 and alone > 1e3 * held_err
