@@ -344,10 +344,13 @@ def run_batched(args):
         b.set_positions(R0)
 
         def step(t):
-            b.propose(t, eta[t], 0.5, bufs["rnew"])
-            b.ratio_into(t, bufs["rnew"], bufs["ratio"], bufs["grad"], bufs["lap"])
-            b.metropolis(u[t], bufs["ratio"], bufs["acc"])
-            b.accept(t, bufs["acc"])
+            if args.separate:
+                b.propose(t, eta[t], 0.5, bufs["rnew"])
+                b.ratio_into(t, bufs["rnew"], bufs["ratio"], bufs["grad"], bufs["lap"])
+                b.metropolis(u[t], bufs["ratio"], bufs["acc"])
+                b.accept(t, bufs["acc"])
+            else:  # msd_step: one persistent launch per group of systems (grid sizes tuned on warm-up)
+                b.step(t, eta[t], 0.5, u[t], bufs["ratio"], bufs["grad"], bufs["lap"], bufs["acc"])
 
         for t in range(args.warmup):
             step(t)
@@ -408,7 +411,11 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": batched_desc(systems, W // len(systems)),
                        "precision": "mixed", "parallelism": f"replicas x{ws}, systems on 8 streams",
+                       "path": ("separate calls: proposal, orbitals, ratio, Metropolis, accept" if args.separate else
+                                "msd_step: one persistent launch per shared-memory group of systems, device "
+                                "work queue, grid size tuned on the warm-up steps"),
                        "l2": "inputs exceed L2"},
+            "launches_per_step": n_launch / args.steps,
             "roofline": roof, "gpu_launches": int(n_launch), "clocks": clocks, "status": flagged or "ok"}
     if args.rescue_slots > 0:
         steps_r = min(args.steps, args.rescue_steps)
@@ -813,6 +820,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--walkers", type=int, default=0, help="override the workload's walker count (profiling)")
     ap.add_argument("--systems", type=int, default=256, help="systems of the batched workload")
+    ap.add_argument("--separate", action="store_true", help="batched workload: the separate calls instead of msd_step")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

@@ -190,6 +190,20 @@ msd_status msd_copy_state(msd_ctx* ctx, int32_t item, int32_t spin, void* dst_de
 msd_status msd_propose(msd_ctx* ctx, int32_t elec, const double* eta_dev, double tau, double* rnew_dev);
 msd_status msd_metropolis(msd_ctx* ctx, const double* u_dev, const double* ratio_dev, uint8_t* accept_dev);
 
+/* One Metropolis step of every walker (Section II: a step moves one electron): the proposal
+ * r' = R[w][elec] + tau * eta_dev[w], ratio_dev [W], grad_dev [W][3] and lap_dev [W] at r' as
+ * msd_ratio gives them, the decision accept_dev[w] = (u_dev[w] < ratio_dev[w]^2) (no Jastrow
+ * factor), and msd_accept of it.  Every pointer is required.  A single-system context runs the
+ * separate calls.  A batched context (elec = electron elec mod n_tot_s of system s) runs the
+ * bookkeeping of msd_ratio, then ONE persistent launch per shared-memory group of systems.  Its
+ * blocks take (system, walker) items from a device counter, largest systems first, and do the whole
+ * step per walker: proposal, orbitals at r' (SIMT, in the path's precision), sweep, decision and
+ * update.  The first calls on a batch time three grid sizes per group with CUDA events (and
+ * synchronise); later calls use the fastest.  A batch with walkers held in FP64 (msd_set_rescue)
+ * runs the separate calls. */
+msd_status msd_step(msd_ctx* ctx, int32_t elec, const double* eta_dev, double tau, const double* u_dev,
+                    double* ratio_dev, double* grad_dev, double* lap_dev, uint8_t* accept_dev);
+
 /* Host-buffer twins of one walker-move, for callers without device memory: copy the
  * inputs to the device, run, copy the results back, synchronise.
  * msd_ratio_host: rnew_host [W][3] -> ratio_host [W], grad_host [W][3], lap_host [W].

@@ -187,6 +187,16 @@ struct msd_ctx {
     BatchPlan bplan;                                        // single-launch descriptors of the systems
     double* b_rnew = nullptr;                               // [W][3] positions of the current proposal
     int* b_status_scratch = nullptr;                        // status word of the FP32 batched ratio launch
+    // the fused step of a batch: blocks per group, chosen by timing candidate grids on the first calls
+    struct StepTuning {
+        std::vector<int> candidates[BatchPlan::kMaxGroups];
+        int chosen[BatchPlan::kMaxGroups] = {0};
+        std::vector<float> ms[BatchPlan::kMaxGroups];
+        int calls = 0;
+        bool done = false;
+        cudaEvent_t ev[2 * BatchPlan::kMaxGroups] = {};
+    } tune;
+    double* step_rnew = nullptr;                            // [W][3] proposal of msd_step (single system)
     std::vector<void*> allocs;
     std::string err;
     // measurement: kernel launch count and events around the excitation-sweep kernel
@@ -1037,6 +1047,29 @@ msd_status build_batch_plan(msd_ctx* c) {
         P.n_groups++;
         P.gfirst[P.n_groups] = (int)blk.size();
     }
+    // fused step: the same groups, systems in decreasing order of work (strings x electrons), so the
+    // persistent blocks finish the large ones first and the small ones fill the tail
+    std::vector<int2> items;
+    for (int g = 0; g < P.n_groups; ++g) {
+        std::vector<int> qs;
+        for (int b = P.gfirst[g]; b < P.gfirst[g + 1]; ++b)
+            if (qs.empty() || qs.back() != blk[b].x) qs.push_back(blk[b].x);
+        size_t sm = 0;
+        for (int q : qs) {
+            const msd_ctx* sc = c->sub[q];
+            const size_t chi = (size_t)NCH * sc->nb * sc->tb;
+            for (int sp = 0; sp < 2; ++sp)
+                sm = std::max(sm, std::max(sys_smem[q], std::max(chi, accept_smem_bytes(sc->sp[sp].n))));
+        }
+        auto work = [&](int q) {
+            const msd_ctx* sc = c->sub[q];
+            return (double)(sc->sp[0].g.n_exc + sc->sp[1].g.n_exc) * (sc->sp[0].n + sc->sp[1].n);
+        };
+        std::stable_sort(qs.begin(), qs.end(), [&](int a, int b) { return work(a) > work(b); });
+        for (int q : qs)
+            for (int w = 0; w < c->sub[q]->W; ++w) items.push_back(make_int2(q, w));
+        P.step_smem[g] = sm;
+    }
     BatchSys* d_sys = nullptr;
     int2* d_blk = nullptr;
     int4* d_tiles = nullptr;
@@ -1052,6 +1085,15 @@ msd_status build_batch_plan(msd_ctx* c) {
         c->bplan.tc_smem = tc_smem;
     }
     TRY(upload(c, &d_wsys, wsys.data(), wsys.size()));
+    {
+        int2* d_items = nullptr;
+        TRY(upload(c, &d_items, items.data(), items.size()));
+        c->bplan.items = d_items;
+        std::vector<int> zeros(2 * BatchPlan::kMaxGroups, 0);
+        int* d_cnt = nullptr;
+        TRY(upload(c, &d_cnt, zeros.data(), zeros.size()));
+        c->bplan.counters = d_cnt;
+    }
     TRY(dalloc(c, &c->b_rnew, (size_t)c->W * 3));
     c->bplan.sys = d_sys;
     c->bplan.n_sys = ns;
@@ -1068,11 +1110,9 @@ msd_status build_batch_plan(msd_ctx* c) {
 // Per-system bookkeeping of a batched msd_ratio (refresh, CI weights: launched on the internal
 // streams between a fork and a join when a system needs them), then one launch each for the
 // orbitals at r' and the ratio of every system.
-msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
-                       double* lap_dev) {
-    if ((grad_dev == nullptr) != (lap_dev == nullptr))
-        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
-    const int nch = grad_dev ? NCH : 1;
+// Per-system bookkeeping before move `elec` of a batch (refresh every K moves of a spin, CI
+// weights when the moving spin changed), on the internal streams; marks the proposal as made.
+msd_status batch_prepare(msd_ctx* c, int elec, int nch) {
     bool forked = false;
     for (size_t q = 0; q < c->sub.size(); ++q) {
         msd_ctx* sc = c->sub[q];
@@ -1105,6 +1145,15 @@ msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* rat
         sc->prop_valid = true;
     }
     if (forked) TRY(batch_join(c));
+    return MSD_OK;
+}
+
+msd_status batch_ratio(msd_ctx* c, int elec, const double* rnew_dev, double* ratio_dev, double* grad_dev,
+                       double* lap_dev) {
+    if ((grad_dev == nullptr) != (lap_dev == nullptr))
+        return fail(c, MSD_ERR_ARG, "grad_dev and lap_dev must be both NULL or both set");
+    const int nch = grad_dev ? NCH : 1;
+    TRY(batch_prepare(c, elec, nch));
     const cudaError_t e = cudaMemcpyAsync(c->b_rnew, rnew_dev, sizeof(double) * 3 * c->W, cudaMemcpyDeviceToDevice,
                                           c->stream);
     if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "copy of rnew: %s", cudaGetErrorString(e));
@@ -1171,6 +1220,73 @@ msd_status batch_accept(msd_ctx* c, int elec, const uint8_t* accept_dev) {
     return MSD_OK;
 }
 
+// Candidate grids of the fused step per group: a persistent grid at the occupancy limit, half of
+// it, and one block per item (the counter then hands each block one item).
+void step_candidates(msd_ctx* c) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int g = 0; g < c->bplan.n_groups; ++g) {
+        const int n = c->bplan.gfirst[g + 1] - c->bplan.gfirst[g];
+        const int occ = std::max(1, step_blocks_per_sm(c->mixed, c->bplan.step_smem[g]));
+        std::vector<int> cand = {std::min(n, occ * sms), std::min(n, std::max(1, occ * sms / 2)), n};
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        c->tune.candidates[g] = cand;
+        c->tune.chosen[g] = cand.front();
+    }
+}
+
+// One Metropolis step of every system: bookkeeping, then one persistent launch per group (the first
+// calls time each candidate grid with events and keep the fastest per group), then the
+// finiteness check of the FP32 path.
+msd_status batch_step(msd_ctx* c, int elec, const double* eta_dev, double tau, const double* u_dev, double* ratio_dev,
+                      double* grad_dev, double* lap_dev, uint8_t* accept_dev) {
+    TRY(batch_prepare(c, elec, NCH));
+    auto& T = c->tune;
+    if (T.candidates[0].empty()) step_candidates(c);
+    const bool tuning = !T.done;
+    const int k = T.calls;
+    if (tuning && !T.ev[0])
+        for (int i = 0; i < 2 * BatchPlan::kMaxGroups; ++i) cudaEventCreate(&T.ev[i]);
+    for (int g = 0; g < c->bplan.n_groups; ++g) {
+        int grid = T.chosen[g];
+        if (tuning) grid = T.candidates[g][std::min<size_t>(k, T.candidates[g].size() - 1)];
+        if (tuning) cudaEventRecord(T.ev[2 * g], c->stream);
+        launch_step_batched(c->L(), c->mixed, c->bplan, g, grid, elec, eta_dev, tau, u_dev, ratio_dev, grad_dev,
+                            lap_dev, accept_dev, c->b_rnew);
+        if (tuning) cudaEventRecord(T.ev[2 * g + 1], c->stream);
+    }
+    TRY(check_launch(c, "batched step"));
+    if (tuning) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(c, MSD_ERR_CUDA, "step tuning: %s", cudaGetErrorString(e));
+        size_t longest = 0;
+        for (int g = 0; g < c->bplan.n_groups; ++g) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, T.ev[2 * g], T.ev[2 * g + 1]);
+            if ((size_t)k < T.candidates[g].size()) T.ms[g].push_back(ms);
+            longest = std::max(longest, T.candidates[g].size());
+        }
+        if ((size_t)++T.calls >= longest) {
+            for (int g = 0; g < c->bplan.n_groups; ++g) {
+                size_t best = 0;
+                for (size_t i = 1; i < T.ms[g].size(); ++i)
+                    if (T.ms[g][i] < T.ms[g][best]) best = i;
+                T.chosen[g] = T.candidates[g][best];
+            }
+            T.done = true;
+        }
+    }
+    if (c->mixed) launch_check_finite_batched(c->L(), c->bplan, c->W, ratio_dev);
+    for (msd_ctx* sc : c->sub) {
+        const int s = spin_of(sc, elec % sc->n_tot);
+        sc->st.C_valid[1 - s] = false;
+        sc->prop_valid = false;
+    }
+    return check_launch(c, "batched step");
+}
+
 msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
     for (int s = 0; s < n_systems; ++s) {
         const msd_status st = validate(p + s);
@@ -1213,6 +1329,7 @@ msd_status batch_init(const msd_problem* p, int n_systems, msd_ctx** out) {
     }
     c->W = (int)w;
     if (dalloc(c, &c->b_status_scratch, 1) != MSD_OK) return bail(MSD_ERR_OOM);
+    if (dalloc(c, &c->step_rnew, (size_t)c->W * 3) != MSD_OK) return bail(MSD_ERR_OOM);
     if (build_batch_plan(c) != MSD_OK) return bail(MSD_ERR_CUDA);
     *out = c;
     return MSD_OK;
@@ -1299,6 +1416,7 @@ msd_status msd_init(const msd_problem* p, int32_t n_systems, msd_ctx** out) {
     if ((st = dalloc(c, &c->num, W * NCH)) != MSD_OK) return bail(st);
     if ((st = valloc(c, &c->y0, W * mmax * c->tb)) != MSD_OK) return bail(st);
     if ((st = dalloc(c, &c->rnew, W * 3)) != MSD_OK) return bail(st);
+    if ((st = dalloc(c, &c->step_rnew, W * 3)) != MSD_OK) return bail(st);
     if ((st = dalloc(c, &c->dummy, W)) != MSD_OK) return bail(st);
     if ((st = dalloc(c, &c->d_io, W * 8)) != MSD_OK) return bail(st);
     if ((st = dalloc(c, &c->d_acc, W)) != MSD_OK) return bail(st);
@@ -1620,6 +1738,29 @@ msd_status msd_metropolis(msd_ctx* c, const double* u_dev, const double* ratio_d
     if (!c || !u_dev || !ratio_dev || !accept_dev) return fail(c, MSD_ERR_ARG, "NULL argument");
     launch_metropolis(c->L(), c->W, u_dev, ratio_dev, accept_dev);
     return check_launch(c, "metropolis");
+}
+
+msd_status msd_step(msd_ctx* c, int32_t elec, const double* eta_dev, double tau, const double* u_dev,
+                    double* ratio_dev, double* grad_dev, double* lap_dev, uint8_t* accept_dev) {
+    if (!c || !eta_dev || !u_dev || !ratio_dev || !grad_dev || !lap_dev || !accept_dev)
+        return fail(c, MSD_ERR_ARG, "NULL argument");
+    if (elec < 0) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    if (c->canon) return fail(c, MSD_ERR_ARG, "not available for the canonical method");
+    if (is_batch(c)) {
+        bool held = false;
+        for (const msd_ctx* sc : c->sub) held = held || rescue_on(sc);
+        if (!held) return batch_step(c, elec, eta_dev, tau, u_dev, ratio_dev, grad_dev, lap_dev, accept_dev);
+        // walkers held in FP64: the separate calls, which serve them
+        TRY(msd_propose(c, elec, eta_dev, tau, c->step_rnew));
+        TRY(msd_ratio(c, elec, c->step_rnew, ratio_dev, grad_dev, lap_dev));
+        TRY(msd_metropolis(c, u_dev, ratio_dev, accept_dev));
+        return msd_accept(c, elec, accept_dev);
+    }
+    if (elec >= c->n_tot) return fail(c, MSD_ERR_ARG, "electron %d out of range", elec);
+    TRY(msd_propose(c, elec, eta_dev, tau, c->step_rnew));
+    TRY(msd_ratio(c, elec, c->step_rnew, ratio_dev, grad_dev, lap_dev));
+    TRY(msd_metropolis(c, u_dev, ratio_dev, accept_dev));
+    return msd_accept(c, elec, accept_dev);
 }
 
 msd_status msd_ratio_host(msd_ctx* c, int32_t elec, const double* rnew_host, double* ratio_host, double* grad_host,

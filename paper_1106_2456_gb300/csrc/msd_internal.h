@@ -205,7 +205,18 @@ struct BatchPlan {
     const int4* tc_tiles = nullptr;
     int n_tc_tiles = 0;
     size_t tc_smem = 0;
+    // the fused Metropolis step (launch_step_batched): (system, walker) items per group, ordered by
+    // decreasing cost, the group's shared memory and a pair of counters per group (zero between launches)
+    const int2* items = nullptr;
+    size_t step_smem[kMaxGroups] = {0};
+    int* counters = nullptr;
 };
+// One Metropolis step of group `group`'s walkers as one persistent launch of `grid` blocks.
+void launch_step_batched(const Launch& L, bool mixed, const BatchPlan& P, int group, int grid, int t,
+                         const double* eta, double tau, const double* u, double* ratio, double* grad, double* lap,
+                         uint8_t* accept, double* rnew);
+// Blocks of the step kernel an SM holds with `smem` bytes of shared memory.
+int step_blocks_per_sm(bool mixed, size_t smem);
 void launch_orbitals_batched(const Launch& L, bool mixed, const BatchPlan& P, int t, int nch, const double* rnew);
 void launch_orbitals_tc_batched(const Launch& L, const BatchPlan& P, int t, int nch, const double* rnew);
 int tc_tile_points(int nch);  // points per tensor-core tile for 1 or 5 channels

@@ -1177,6 +1177,100 @@ __global__ void __launch_bounds__(kBlock) k_accept_batched(const BatchSys* __res
     accept_block<TO, TT>(sa, bw.y, s_status);
 }
 
+// ------------------------------------------------------------------------------------------
+// One Metropolis step of every walker of every system in one persistent launch per group of
+// systems: a block takes (system, walker) items from a device counter until none is left and, for
+// each, proposes r' = r + tau eta, evaluates the moving spin's orbitals at r' (SIMT, all five
+// channels), runs the ratio sweep (ratio_block), takes the Metropolis decision u < ratio^2 and
+// applies the update (accept_block).  The last block to run out resets the counter for the next
+// launch (no block waits on another).
+// ------------------------------------------------------------------------------------------
+template <typename TO>
+__device__ __forceinline__ void orbitals_walker(const double* rp, const double4* __restrict__ bas,
+                                                const int8_t* __restrict__ blm, int nb, const TO* __restrict__ Bm,
+                                                int N, TO* __restrict__ out, TO* chi) {
+    for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) {
+        TO v[5];
+        basis_channels<TO>(rp, bas[mu], blm[mu], v);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) chi[a * nb + mu] = v[a];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        TO acc[5] = {TO(0), TO(0), TO(0), TO(0), TO(0)};
+        for (int mu = 0; mu < nb; ++mu) {
+            const TO b = __ldg(Bm + (long long)mu * N + j);
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc[a] = fma(chi[a * nb + mu], b, acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) out[a * N + j] = acc[a];
+    }
+}
+
+template <typename TO, typename TT>
+__global__ void __launch_bounds__(kBlock, sizeof(TT) == 4 ? MSD_RATIO_F32_BLOCKS : 2)
+    k_step_batched(const BatchSys* __restrict__ sys, const int2* __restrict__ items, int n_items, int t,
+                   const double* __restrict__ eta, double tau, const double* __restrict__ u, double* ratio,
+                   double* grad, double* lap, uint8_t* accept, double* rnew, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ RatioArgs sa;
+    __shared__ AcceptArgs sb;
+    __shared__ int* s_rstatus;
+    __shared__ int* s_status;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 sw = items[it];
+        const BatchSys& B = sys[sw.x];
+        const int w = sw.y, gw = B.w_off + w;
+        int e;
+        const int sp = batch_spin(B, t, e);
+        if (tid < 3) rnew[3LL * gw + tid] = fma(tau, eta[3LL * gw + tid], B.R[((long long)w * B.n_tot + e) * 3 + tid]);
+        if (tid == 0) {
+            sa = B.ratio[sp];
+            sa.row = e - (sp ? B.n_up : 0);
+            sa.nch = NCH;
+            sa.ratio = ratio + B.w_off;
+            sa.rs = 1;
+            sa.grad = grad + 3LL * B.w_off;
+            sa.gs = 3;
+            sa.lap = lap + B.w_off;
+            sa.ls = 1;
+            sb = B.accept[sp];
+            sb.row = sa.row;
+            sb.elec = e;
+            sb.nch = NCH;
+            sb.accept = accept + B.w_off;
+            sb.rnew = rnew + 3LL * B.w_off;
+            s_rstatus = B.ratio_status ? B.ratio_status : B.status;
+            s_status = B.status;
+        }
+        __syncthreads();
+        const OrbArgs& o = B.orb[sp];
+        orbitals_walker<TO>(rnew + 3LL * gw, o.bas, o.blm, o.nb, static_cast<const TO*>(o.B), o.N,
+                            static_cast<TO*>(o.out) + (long long)w * NCH * o.N, reinterpret_cast<TO*>(smem));
+        __syncthreads();
+        ratio_block<TO, TT, NCH>(sa, w, s_rstatus);
+        __syncthreads();
+        if (tid == 0) {
+            const double r = ratio[gw];
+            accept[gw] = (u[gw] < r * r) ? 1 : 0;
+        }
+        __syncthreads();
+        accept_block<TO, TT>(sb, w, s_status);
+        __syncthreads();
+    }
+    if (tid == 0 && atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {
+        counter[0] = 0;  // every block has left the loop: no item is taken any more in this launch
+        counter[1] = 0;
+    }
+}
+
 __global__ void k_propose_batched(const BatchSys* __restrict__ sys, const int* __restrict__ wsys, int Wt, int t,
                                   const double* __restrict__ eta, double tau, double* __restrict__ rnew) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1483,6 +1577,38 @@ void launch_propose_batched(const Launch& L, const BatchPlan& P, int W_total, in
                             double* rnew) {
     L.count();
     k_propose_batched<<<(W_total * 3 + 255) / 256, 256, 0, L.stream>>>(P.sys, P.wsys, W_total, t, eta, tau, rnew);
+}
+
+template <typename TO, typename TT>
+static void step_batched_impl(const Launch& L, const BatchPlan& P, int group, int grid, int t, const double* eta,
+                              double tau, const double* u, double* ratio, double* grad, double* lap, uint8_t* accept,
+                              double* rnew) {
+    const int first = P.gfirst[group], n = P.gfirst[group + 1] - first;
+    if (n <= 0) return;
+    const size_t sm = P.step_smem[group];
+    set_smem(k_step_batched<TO, TT>, sm);
+    L.count();
+    k_step_batched<TO, TT><<<grid, kBlock, sm, L.stream>>>(P.sys, P.items + first, n, t, eta, tau, u, ratio, grad, lap,
+                                                          accept, rnew, P.counters + 2 * group);
+}
+
+void launch_step_batched(const Launch& L, bool mixed, const BatchPlan& P, int group, int grid, int t,
+                         const double* eta, double tau, const double* u, double* ratio, double* grad, double* lap,
+                         uint8_t* accept, double* rnew) {
+    if (mixed) step_batched_impl<float, float>(L, P, group, grid, t, eta, tau, u, ratio, grad, lap, accept, rnew);
+    else step_batched_impl<double, double>(L, P, group, grid, t, eta, tau, u, ratio, grad, lap, accept, rnew);
+}
+
+int step_blocks_per_sm(bool mixed, size_t smem) {
+    int b = 0;
+    if (mixed) {
+        set_smem(k_step_batched<float, float>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batched<float, float>, kBlock, smem);
+    } else {
+        set_smem(k_step_batched<double, double>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batched<double, double>, kBlock, smem);
+    }
+    return b;
 }
 
 size_t accept_smem_bytes(int n) {

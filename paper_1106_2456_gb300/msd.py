@@ -112,6 +112,7 @@ def load_library():
         "msd_selftest_wait": ([vp, ctypes.c_int64], i32),
         "msd_set_rescue": ([vp, i32, ctypes.c_double, ctypes.c_double], i32),
         "msd_rescue_stats": ([vp, vp], i32),
+        "msd_step": ([vp, i32, vp, ctypes.c_double, vp, vp, vp, vp, vp], i32),
         "msd_set_hamiltonian": ([vp, vp, vp], i32),
         "msd_jastrow_ratio": ([vp, i32, vp, vp], i32),
         "msd_local_energy": ([vp, vp, vp], i32),
@@ -342,6 +343,15 @@ class MSD:
         self.local_energy_into(e, parts)
         return (e, parts) if with_parts else e
 
+    def step(self, elec: int, eta: torch.Tensor, tau: float, u: torch.Tensor, ratio: torch.Tensor,
+             grad: torch.Tensor, lap: torch.Tensor, accept: torch.Tensor):
+        """msd_step: proposal, ratio/grad/lap, Metropolis decision and update of every walker."""
+        W = self.W
+        self._check(self.lib.msd_step(self.ctx, int(elec), _dptr(eta, torch.float64, (W, 3), "eta"), float(tau),
+                                      _dptr(u, torch.float64, (W,), "u"), _dptr(ratio, torch.float64, (W,), "ratio"),
+                                      _dptr(grad, torch.float64, (W, 3), "grad"), _dptr(lap, torch.float64, (W,), "lap"),
+                                      _dptr(accept, torch.uint8, (W,), "accept")))
+
     def metropolis(self, u: torch.Tensor, ratio: torch.Tensor, out: torch.Tensor):
         self._check(self.lib.msd_metropolis(self.ctx, _dptr(u, torch.float64, (self.W,), "u"),
                                             _dptr(ratio, torch.float64, (self.W,), "ratio"),
@@ -501,6 +511,15 @@ class MSDBatch:
         l = self._empty(self.W) if with_grad else None
         self.ratio_into(elec, rnew, r, g, l)
         return r, g, l
+
+    def step(self, elec: int, eta: torch.Tensor, tau: float, u: torch.Tensor, ratio: torch.Tensor,
+             grad: torch.Tensor, lap: torch.Tensor, accept: torch.Tensor):
+        """msd_step: proposal, ratio/grad/lap, Metropolis decision and update of every walker."""
+        W = self.W
+        self._check(self.lib.msd_step(self.ctx, int(elec), _dptr(eta, torch.float64, (W, 3), "eta"), float(tau),
+                                      _dptr(u, torch.float64, (W,), "u"), _dptr(ratio, torch.float64, (W,), "ratio"),
+                                      _dptr(grad, torch.float64, (W, 3), "grad"), _dptr(lap, torch.float64, (W,), "lap"),
+                                      _dptr(accept, torch.uint8, (W,), "accept")))
 
     def metropolis(self, u: torch.Tensor, ratio: torch.Tensor, out: torch.Tensor):
         self._check(self.lib.msd_metropolis(self.ctx, _dptr(u, torch.float64, (self.W,), "u"),

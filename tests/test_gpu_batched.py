@@ -110,3 +110,72 @@ def test_batch_against_oracle_and_backward():
         pb += nB
         c.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol,steps", [("fp64", 1e-10, 30), ("mixed", 1e-3, 8)])
+def test_fused_step_matches_separate_calls(prec, tol, steps):
+    """msd_step on a batch (one persistent launch per group: proposal, SIMT orbitals, sweep,
+    decision, update per walker; grid sizes tuned on the first calls) against the separate calls
+    (proposal, tensor-core or SIMT orbitals, ratio, Metropolis, accept) on the same random numbers:
+    the same decisions, positions and log|Psi|, and ratios within the path's rounding."""
+    ws = _systems()
+    Ks = [w.refresh_K for w in ws]
+    mk = lambda: msd.MSDBatch([w.problem for w in ws], [w.n_walkers for w in ws], prec, refresh_K=Ks)
+    a, b = mk(), mk()
+    R = torch.tensor(np.concatenate([w.R0.reshape(-1) for w in ws]), device="cuda")
+    a.set_positions(R)
+    b.set_positions(R)
+    W = a.W
+    rng = np.random.default_rng(21)
+    f64 = lambda *sh: torch.empty(*sh, dtype=torch.float64, device="cuda")
+    for t in range(steps):
+        eta = torch.tensor(rng.standard_normal((W, 3)), device="cuda")
+        u = torch.tensor(rng.random(W), device="cuda")
+        r1, g1, l1, acc1 = f64(W), f64(W, 3), f64(W), torch.empty(W, dtype=torch.uint8, device="cuda")
+        a.step(t, eta, 0.4, u, r1, g1, l1, acc1)
+        rnew = f64(W, 3)
+        b.propose(t, eta, 0.4, rnew)
+        r2, g2, l2 = b.ratio(t, rnew)
+        acc2 = torch.empty(W, dtype=torch.uint8, device="cuda")
+        b.metropolis(u, r2, acc2)
+        b.accept(t, acc2)
+        for x, y in ((r1, r2), (g1, g2), (l1, l2)):
+            assert bool(((x - y).abs() <= tol * y.abs().clamp_min(1.0)).all()), (prec, t)
+        assert torch.equal(acc1, acc2), (prec, t)
+    a.sync()
+    b.sync()
+    Ra, la, sa = a.get_state()
+    Rb, lb, sb = b.get_state()
+    assert torch.equal(Ra, Rb) and torch.equal(sa, sb)
+    assert torch.allclose(la, lb, rtol=0, atol=1e-9 if prec == "fp64" else 1e-3)
+    a.close()
+    b.close()
+
+
+def test_single_system_step_equals_separate_calls():
+    w = wl.make_workload("water", n_walkers=24)
+    p = w.problem
+    a = msd.MSD(p, w.n_walkers, "mixed", refresh_K=w.refresh_K)
+    b = msd.MSD(p, w.n_walkers, "mixed", refresh_K=w.refresh_K)
+    R = torch.tensor(w.R0, device="cuda")
+    a.set_positions(R)
+    b.set_positions(R)
+    eta_all, u_all = w.proposals(12)
+    W = w.n_walkers
+    f64 = lambda *sh: torch.empty(*sh, dtype=torch.float64, device="cuda")
+    for t in range(12):
+        e = t % p.n_tot
+        eta = torch.tensor(eta_all[t], device="cuda")
+        u = torch.tensor(u_all[t], device="cuda")
+        r1, g1, l1, acc1 = f64(W), f64(W, 3), f64(W), torch.empty(W, dtype=torch.uint8, device="cuda")
+        a.step(e, eta, w.tau, u, r1, g1, l1, acc1)
+        rnew = f64(W, 3)
+        b.propose(e, eta, w.tau, rnew)
+        r2, g2, l2 = b.ratio(e, rnew)
+        acc2 = torch.empty(W, dtype=torch.uint8, device="cuda")
+        b.metropolis(u, r2, acc2)
+        b.accept(e, acc2)
+        assert torch.equal(acc1, acc2)
+        assert torch.allclose(r1, r2, rtol=1e-6, atol=0)
+    a.close()
+    b.close()
