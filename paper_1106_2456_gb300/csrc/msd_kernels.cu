@@ -674,53 +674,112 @@ constexpr int kWarps = kBlock / 32;
 #endif
 constexpr int kSweepDepth = MSD_SWEEP_DEPTH;  // batches of loads in flight per warp
 
+// Orders 1 and 2 take kUnroll12 batches per iteration, orders 3..kUnrollK two: independent
+// eliminations whose shared-memory gathers and arithmetic overlap.
+#ifndef MSD_UNROLL12
+#define MSD_UNROLL12 4
+#endif
+#ifndef MSD_UNROLL_KMAX
+#define MSD_UNROLL_KMAX 2
+#endif
+constexpr int kUnroll12 = MSD_UNROLL12;
+constexpr int kUnrollK = MSD_UNROLL_KMAX;
+
+template <int K>
+__device__ __forceinline__ typename RecRaw<K>::type empty_raw() {
+    using Raw = typename RecRaw<K>::type;
+    if constexpr (K == 1) return Raw(0xffffu);
+    else if constexpr (K == 2) return Raw(0xffffffffu);
+    else if constexpr (K <= 4) return make_uint2(0xffffffffu, 0xffffffffu);
+    else return make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+}
+
 template <int K, typename TT, int NGW>
 __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int ld, const TT* xs,
-                                            const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int base) {
+                                            const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int first) {
+    constexpr int U = K <= 2 ? kUnroll12 : K <= kUnrollK ? 2 : 1;  // batches per iteration
+    constexpr int QD = U * ((kSweepDepth + U - 1) / U);            // batches of loads in flight
     const int j0 = g.goff[K], j1 = g.goff[K + 1];
     const uint8_t* rec = g.rec + g.roff[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     TT* Gmine = Gw + (warp % NGW) * ld;
-    // Warps take the group's batches of 32 strings round-robin, numbered across all groups from
-    // `base` on, so the batches left over at the end of a group fall on different warps.
+    // Warps take the group's batches of 32 strings round-robin, numbered on from the `first`
+    // batches of the groups swept before, so the batches left over at the end of a group fall
+    // on different warps.
     const int nb = (j1 - j0) / kBatch;
-    int b = (warp - ((j0 - base) / kBatch) % nw + nw) % nw;
-    // kSweepDepth batches of record and C loads in flight ahead of the arithmetic
+    int b = (warp - first % nw + nw) % nw;
+    // record and C loads of the next QD batches in flight ahead of the arithmetic; a batch past
+    // the group's end reads as empty records
     using Raw = typename RecRaw<K>::type;
-    Raw rq[kSweepDepth];
-    TT cq[kSweepDepth];
+    Raw rq[QD];
+    TT cq[QD];
 #pragma unroll
-    for (int i = 0; i < kSweepDepth; ++i) {
+    for (int i = 0; i < QD; ++i) {
         const int bi = b + i * nw;
-        rq[i] = Raw{};
+        rq[i] = empty_raw<K>();
         cq[i] = TT(0);
         if (bi < nb) {
             rq[i] = load_raw<K>(rec, bi * kBatch + lane);
             cq[i] = __ldcs(Cw + j0 + bi * kBatch + lane);
         }
     }
-    for (; b < nb; b += nw) {
-        const Raw rc = rq[0];
-        const TT cu = cq[0];
+    for (; b < nb; b += U * nw) {
+        Raw rc[U];
+        TT cu[U];
 #pragma unroll
-        for (int i = 0; i + 1 < kSweepDepth; ++i) {
-            rq[i] = rq[i + 1];
-            cq[i] = cq[i + 1];
+        for (int i = 0; i < U; ++i) {
+            rc[i] = rq[i];
+            cu[i] = cq[i];
         }
-        const int bn = b + kSweepDepth * nw;
-        if (bn < nb) {
-            rq[kSweepDepth - 1] = load_raw<K>(rec, bn * kBatch + lane);
-            cq[kSweepDepth - 1] = __ldcs(Cw + j0 + bn * kBatch + lane);
-        }
-        int h[K], p[K];
-        decode_rec<K>(rc, h, p);
-        if (h[0] != kEmptyRecord) {
-            TT det, z[K];
-            adj_solve<K, TT>(Ts, ld, xs, h, p, det, z);
-            sacc.add(0, cu * det);
-            // the batch's particles in any one slot lie in distinct banks: no conflicts
 #pragma unroll
-            for (int l = 0; l < K; ++l) atomicAdd(Gmine + p[l], cu * z[l]);
+        for (int i = 0; i + U < QD; ++i) {
+            rq[i] = rq[i + U];
+            cq[i] = cq[i + U];
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int bn = b + (QD + i) * nw;
+            rq[QD - U + i] = empty_raw<K>();
+            cq[QD - U + i] = TT(0);
+            if (bn < nb) {
+                rq[QD - U + i] = load_raw<K>(rec, bn * kBatch + lane);
+                cq[QD - U + i] = __ldcs(Cw + j0 + bn * kBatch + lane);
+            }
+        }
+        int h[U][K], p[U][K];
+        bool live[U];
+        TT det[U], z[U][K];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            decode_rec<K>(rc[i], h[i], p[i]);
+            live[i] = h[i][0] != kEmptyRecord;
+            det[i] = TT(0);
+#pragma unroll
+            for (int l = 0; l < K; ++l) z[i][l] = TT(0);
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i)
+            if (live[i]) {
+                adj_solve<K, TT>(Ts, ld, xs, h[i], p[i], det[i], z[i]);
+                sacc.add(0, cu[i] * det[i]);
+            }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if constexpr (sizeof(TT) == 4) {
+                // FP32 tables come with conflict-free batches: within a slot the 32 lanes'
+                // particles are distinct, and every warp owns its copy of G, so a plain
+                // read-modify-write per slot, ordered between slots by a warp barrier, needs no
+                // atomics
+#pragma unroll
+                for (int l = 0; l < K; ++l) {
+                    if (live[i]) Gmine[p[i][l]] += cu[i] * z[i][l];
+                    __syncwarp();
+                }
+            } else {
+                if (live[i])
+#pragma unroll
+                    for (int l = 0; l < K; ++l) atomicAdd(Gmine + p[i][l], cu[i] * z[i][l]);
+            }
         }
     }
 }
@@ -730,8 +789,8 @@ __device__ __forceinline__ void sweep_group(const ExcDev& g, const TT* Ts, int l
 // the common orders.
 template <int K, typename TT, int NGW>
 __device__ __noinline__ void sweep_group_outlined(const ExcDev& g, const TT* Ts, int ld, const TT* xs,
-                                                  const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int base) {
-    sweep_group<K, TT, NGW>(g, Ts, ld, xs, Cw, Gw, sacc, base);
+                                                  const TT* __restrict__ Cw, TT* Gw, Accum<TT, 1>& sacc, int first) {
+    sweep_group<K, TT, NGW>(g, Ts, ld, xs, Cw, Gw, sacc, first);
 }
 
 struct RatioSmem {
@@ -865,18 +924,19 @@ __device__ __forceinline__ void ratio_block(const RatioArgs& a, const int w, int
             sacc.add(0, st);
         }
     }
-    const int base = a.g.goff[a.g.dense1 ? 2 : 1];
+    int first = 0;  // batches of the groups swept so far
     for (int k = a.g.dense1 ? 2 : 1; k <= a.g.kmax; ++k) {
         switch (k) {
-            case 1: sweep_group<1, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 2: sweep_group<2, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 3: sweep_group<3, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 4: sweep_group<4, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 5: sweep_group_outlined<5, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 6: sweep_group_outlined<6, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 7: sweep_group_outlined<7, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
-            case 8: sweep_group_outlined<8, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, base); break;
+            case 1: sweep_group<1, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 2: sweep_group<2, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 3: sweep_group<3, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 4: sweep_group<4, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 5: sweep_group_outlined<5, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 6: sweep_group_outlined<6, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 7: sweep_group_outlined<7, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
+            case 8: sweep_group_outlined<8, TT, NGW>(a.g, Ts, m, xs, Cw, Gw, sacc, first); break;
         }
+        first += (a.g.goff[k + 1] - a.g.goff[k]) / kBatch;
     }
     __syncthreads();
     // G = G1 + the per-warp copies, kept in G1

@@ -66,14 +66,29 @@ MSD_HD T dop(T a, T b, T c, T d) {
 // S steps of LU with partial pivoting on the K x K block M, the right-hand side b permuted and
 // eliminated alongside.  On return rows/columns < S hold U with 1/u_kk on the diagonal, the
 // trailing (K-S) x (K-S) block holds the Schur complement, and the return value is
-// sign(P) * prod u_kk.  `singular` is set if a pivot is exactly zero (the column below the
+// sign(P) * prod u_kk, starting from dp.  The first K0 steps take their pivot row as it stands
+// (the caller has already put the pivot there).  `singular` is set if a pivot is exactly zero (the column below the
 // diagonal is then zero and T_u is singular).
-template <int K, int S, typename TT>
-MSD_HD TT lu_steps(TT (&M)[K][K], TT (&b)[K], bool& singular) {
-    TT dp = TT(1);
+template <int K, int S, typename TT, int K0 = 0>
+MSD_HD TT lu_steps(TT (&M)[K][K], TT (&b)[K], bool& singular, TT dp = TT(1)) {
     singular = false;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
+        if (k < K0) {  // pivot already in place (rows ordered before loading)
+            const TT pv = M[k][k];
+            dp *= pv;
+            singular |= (pv == TT(0));
+            const TT ip = recip(pv);
+#pragma unroll
+            for (int r = k + 1; r < K; ++r) {
+                const TT fct = M[r][k] * ip;
+#pragma unroll
+                for (int j = k + 1; j < K; ++j) M[r][j] = fma(-fct, M[k][j], M[r][j]);
+                b[r] = fma(-fct, b[k], b[r]);
+            }
+            M[k][k] = ip;
+            continue;
+        }
         int piv = k;
         TT best = tabs(M[k][k]);
 #pragma unroll
@@ -180,7 +195,7 @@ MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], con
     if constexpr (K == 1) {
         det = Ts[h[0] * ld + p[0]];
         z[0] = xs[h[0]];
-    } else {
+    } else if constexpr (K == 2) {
         TT M[K][K], b[K];
 #pragma unroll
         for (int q = 0; q < K; ++q) {
@@ -188,8 +203,48 @@ MSD_HD void adj_solve(const TT* Ts, int ld, const TT* xs, const int (&h)[K], con
             for (int l = 0; l < K; ++l) M[q][l] = Ts[h[q] * ld + p[l]];
             b[q] = xs[h[q]];
         }
+        det = dop(M[0][0], M[1][1], M[0][1], M[1][0]);
+        z[0] = dop(M[1][1], b[0], M[0][1], b[1]);
+        z[1] = dop(M[0][0], b[1], M[1][0], b[0]);
+    } else {
+        // The first elimination step's row exchange is made on the hole indices before the rest
+        // of T_u is gathered: the first column alone decides the pivot, and exchanging two
+        // holes then costs a few integer selects instead of exchanging K values in every row.
+        TT M[K][K], b[K];
+        int hp[K];
+        TT c0[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) c0[q] = Ts[h[q] * ld + p[0]];
+        int piv = 0;
+        TT best = tabs(c0[0]);
+#pragma unroll
+        for (int r = 1; r < K; ++r) {
+            const TT v = tabs(c0[r]);
+            if (v > best) {
+                best = v;
+                piv = r;
+            }
+        }
+        int h0 = h[0];
+        TT v0 = c0[0];
+#pragma unroll
+        for (int r = 1; r < K; ++r) {
+            const bool sw = piv == r;
+            h0 = sw ? h[r] : h0;
+            v0 = sw ? c0[r] : v0;
+            hp[r] = sw ? h[0] : h[r];
+            M[r][0] = sw ? c0[0] : c0[r];
+        }
+        hp[0] = h0;
+        M[0][0] = v0;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+#pragma unroll
+            for (int l = 1; l < K; ++l) M[q][l] = Ts[hp[q] * ld + p[l]];
+            b[q] = xs[hp[q]];
+        }
         bool singular;
-        const TT dp = lu_steps<K, K - 2, TT>(M, b, singular);
+        const TT dp = lu_steps<K, K - 2, TT, 1>(M, b, singular, piv != 0 ? TT(-1) : TT(1));
         if (singular) {
             int hh[MSD_MAX_ORDER], pp[MSD_MAX_ORDER];
             TT zz[MSD_MAX_ORDER];
