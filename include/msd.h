@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define MSD_MAX_ORDER 8   /* largest per-spin excitation order (Section III: "less then 8") */
+#define MSD_MAX_ORDER 8   /* largest per-spin excitation order (Section III: orders stay below 8) */
 #define MSD_MAX_ORB 256   /* holes and particles are stored as uint8 */
 
 typedef enum {
