@@ -124,6 +124,16 @@ def test_all_orders_ragged(orders):
     _assert(out, MIXED_TOL, "orders 1..8 mixed")
 
 
+@pytest.mark.parametrize("n_det", [100, 2000])
+def test_mixed_fewer_virtuals_than_a_warp(n_det):
+    """FP32 path with m = 16 virtual orbitals per spin (a batch of 32 holds at most 16 strings),
+    37 walkers, geometric orders up to 4-5 with the up spin's singles as records (100
+    determinants) and up to 8 with dense singles (2000), all moves against the oracle."""
+    w = wl.custom_workload((12, 8), (28, 24), n_det, wl.geometric_orders(1, 8), W=37, n_nuc=4, seed=12, K=7)
+    out = replay(w, "mixed", n_steps=w.problem.n_tot)
+    _assert(out, MIXED_TOL, f"m = 16 mixed, {n_det} determinants")
+
+
 def test_single_determinant_and_no_virtuals():
     """n_det = 1 (canonical Slater): ratio = Sherman-Morrison denominator; also N = n."""
     base = wl.make_workload("water", n_walkers=9)
