@@ -179,3 +179,54 @@ def test_single_system_step_equals_separate_calls():
         assert torch.allclose(r1, r2, rtol=1e-6, atol=0)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fused_step_replay_against_oracle(prec):
+    """msd_step on the six-system batch over 2 n_tot steps (every electron of every system moved
+    twice, refreshes and spin changes included): every walker's ratio, gradient and laplacian
+    against the oracle at the positions before the move, element by element under the bar of the
+    precision at that walker's reference condition number, and the final positions replayed on
+    the host from the returned decisions."""
+    ws = _systems()
+    Ks = [w.refresh_K for w in ws]
+    b = msd.MSDBatch([w.problem for w in ws], [w.n_walkers for w in ws], prec, refresh_K=Ks)
+    Rh = [w.R0.copy() for w in ws]
+    b.set_positions(torch.tensor(np.concatenate([r.reshape(-1) for r in Rh]), device="cuda"))
+    orcs = [oracle.Oracle(w.problem) for w in ws]
+    W = b.W
+    off = np.cumsum([0] + [w.n_walkers for w in ws])
+    rng = np.random.default_rng(33)
+    tau = 0.4
+    f64 = lambda *sh: torch.empty(*sh, dtype=torch.float64, device="cuda")
+    tol = tol_fp64 if prec == "fp64" else (lambda k: max(3e-3, 10 * 2.0 ** -24 * k))
+    steps = 2 * max(w.problem.n_tot for w in ws)
+    worst = 0.0
+    for t in range(steps):
+        eta = rng.standard_normal((W, 3))
+        u = rng.random(W)
+        r, g, l, acc = f64(W), f64(W, 3), f64(W), torch.empty(W, dtype=torch.uint8, device="cuda")
+        b.step(t, torch.tensor(eta, device="cuda"), tau, torch.tensor(u, device="cuda"), r, g, l, acc)
+        r, g, l, acc = r.cpu().numpy(), g.cpu().numpy(), l.cpu().numpy(), acc.cpu().numpy()
+        for s, w in enumerate(ws):
+            e = t % w.problem.n_tot
+            sl = slice(off[s], off[s + 1])
+            rnew = Rh[s][:, e] + tau * eta[sl]
+            ref, new = orcs[s].ratio(Rh[s], e, rnew)
+            for i in range(w.n_walkers):
+                kap = orcs[s].reference_condition(Rh[s][i], e, rnew[i])
+                bar = float(tol(kap))
+                errs = (rel_err(r[sl][i], ref[i], new["absum"][i, 0] * abs(ref[i])),
+                        np.max(rel_err(g[sl][i], new["grad"][i], new["absum"][i, 1:4])),
+                        rel_err(l[sl][i], new["lap"][i], new["absum"][i, 4]))
+                worst = max(worst, max(float(x) for x in errs) / bar)
+                assert all(float(x) <= bar for x in errs), (prec, t, s, i, errs, kap)
+            # the decision is u < ratio^2 on the library's own ratio
+            assert np.array_equal(acc[sl].astype(bool), u[sl] < r[sl] ** 2), (prec, t, s)
+            Rh[s][acc[sl].astype(bool), e] = rnew[acc[sl].astype(bool)]
+    b.sync()
+    Rb, _, _ = b.get_state()
+    # the host forms R + tau eta with a separate rounding of the product, the device with fma
+    assert np.max(np.abs(Rb.cpu().numpy() - np.concatenate([x.reshape(-1) for x in Rh]))) <= 1e-13
+    print(f"fused step vs oracle, {prec}: worst error {worst:.3f} of the bar over {steps} steps")
+    b.close()
