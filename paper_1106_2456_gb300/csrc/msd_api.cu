@@ -2071,6 +2071,8 @@ void msd_destroy(msd_ctx* c) {
     }
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tune.ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
